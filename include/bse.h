@@ -1,0 +1,154 @@
+/*
+ * bse.h -- C ABI of the GB300 (sm_103a) solvers for the form-I Bethe-Salpeter
+ * eigenproblem of Benner & Penke, "Efficient and Accurate Algorithms for
+ * Solving the Bethe-Salpeter Eigenvalue Problem for Crystalline Systems"
+ * (arXiv 2008.08825).
+ *
+ * Problem (Eq. (3), Section 1): H1 = [A B; -B -A] with A = A^H, B = B^H, and
+ * A + B, A - B positive definite (Lemma Qtransform item 2).  Then H1 has real
+ * eigenvalues +-omega_i, omega_i > 0 (Thm. 5, Lemma ComputeNegEvecs).  The
+ * solvers return the n positive eigenvalues omega (ascending) and the
+ * eigenvector block V = [X; Y] in C^{2n x n} with H1 V = V diag(omega) and
+ * V^H Sigma V = X^H X - Y^H Y = I (Thm. ProdEig, Eq. (13); Section 4).  The
+ * eigenvector of -omega_i is [Y_i; X_i] (Lemma ComputeNegEvecs) and is not
+ * materialised.
+ *
+ * Conventions for every entry point below:
+ *   - Complex matrices are complex128 stored as interleaved (re, im) doubles,
+ *     column-major: element (i, j) of a matrix with leading dimension ld is at
+ *     p[2*(i + j*ld)] (real) and p[2*(i + j*ld) + 1] (imaginary).  ld >= max(1, n).
+ *   - Unless a name ends in _host, every data pointer is a DEVICE pointer,
+ *     allocated and owned by the caller.  Inputs are never modified.
+ *   - Only the lower triangle (diagonal included) of the Hermitian inputs A, B
+ *     is read; the imaginary parts of their diagonals are ignored.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; the call then synchronises that stream, reads the
+ *     device-side status word and returns it.  Outputs are written only when
+ *     the status is BSE_OK.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ *   - On any status other than BSE_OK, bse_last_error() gives a message.
+ */
+#ifndef BSE_GB300_H
+#define BSE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_ERR_ARG = 1,              /* invalid argument (size, leading dimension, NULL pointer) */
+  BSE_ERR_NOT_PD_AMINUSB = 2,   /* A - B not positive definite; info = failing column (1-based) */
+  BSE_ERR_NOT_PD_APLUSB = 3,    /* A + B not positive definite; info = failing column (1-based) */
+  BSE_ERR_NO_CONVERGENCE = 4,   /* an iteration (bisection, refinement) hit its cap */
+  BSE_ERR_REFINE = 5,           /* mixed-precision refinement did not converge */
+  BSE_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired */
+  BSE_ERR_CUDA = 7,             /* a CUDA runtime call failed (see bse_last_error) */
+  BSE_ERR_NOMEM = 8,            /* workspace allocation failed */
+  BSE_ERR_NOT_IMPLEMENTED = 9   /* option not supported by this build */
+} bse_status;
+
+typedef enum { BSE_PREC_FP64 = 0, BSE_PREC_MIXED = 1 } bse_precision;
+typedef enum { BSE_METHOD_CHOL = 0, BSE_METHOD_SVD = 1 } bse_method;
+
+typedef struct bse_info {
+  int64_t info;          /* failing column (1-based) for NOT_PD, else 0 */
+  double err_est;        /* mixed form: estimated relative eigenvalue error after refinement */
+  int32_t refine_iters;  /* mixed form: refinement sweeps used */
+  int32_t reserved;
+} bse_info;
+
+typedef struct bse_context* bse_handle;
+
+/* Create / destroy a solver context bound to the current CUDA device.  The
+ * context owns a device workspace that grows on demand (cudaMalloc) unless
+ * the caller supplies one with bse_set_workspace. */
+bse_status bse_create(bse_handle* h);
+bse_status bse_destroy(bse_handle h);
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char* bse_last_error(void);
+
+/* Bytes of device workspace a solve of size n needs (method: bse_method;
+ * prec: bse_precision), for all n eigenpairs. */
+bse_status bse_workspace_size(int64_t n, int method, int prec, size_t* bytes);
+
+/* Use caller-owned device memory [ptr, ptr + bytes) as workspace (256-byte
+ * aligned).  The memory must stay valid while the handle uses it; pass
+ * ptr = NULL to return to internally allocated workspace. */
+bse_status bse_set_workspace(bse_handle h, void* ptr, size_t bytes);
+
+/*
+ * Cholesky method, Alg. 2 (Section 3.2):
+ *   L L^H = A - B;  M = L^H (A + B) L;  M V_M = V_M D;  Lambda = D^{1/2};
+ *   V1 = L^{-H} V_M Lambda^{1/2};  V2 = L V_M Lambda^{-1/2};
+ *   X = (V1 + V2)/2,  Y = (V2 - V1)/2.
+ * n        problem size (H1 is 2n x 2n), n >= 0.
+ * A, B     device, n x n Hermitian, lower triangle read, leading dims lda, ldb.
+ * il, iu   1-based inclusive index range into the ascending omega; il = 1,
+ *          iu = n returns all pairs.  k = iu - il + 1 columns are returned.
+ * prec     BSE_PREC_FP64 (all arithmetic FP64).  BSE_PREC_MIXED returns
+ *          BSE_ERR_NOT_IMPLEMENTED in this build.
+ * omega    device, k doubles, ascending.
+ * X, Y     device, n x k complex, leading dims ldx, ldy; both NULL for
+ *          eigenvalues only.
+ * info     host pointer (may be NULL), filled on return.
+ * Errors: BSE_ERR_ARG, BSE_ERR_NOT_PD_AMINUSB (info = column), BSE_ERR_CUDA,
+ *         BSE_ERR_NOMEM, BSE_ERR_NO_CONVERGENCE.
+ */
+bse_status bse_solve_chol(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X,
+                          int64_t ldx, double* Y, int64_t ldy, bse_info* info, void* stream);
+
+/*
+ * SVD method, Alg. 3 (Section 3.3):
+ *   L1 L1^H = A + B;  L2 L2^H = A - B;  U Lambda V^H = L1^H L2 (SVD);
+ *   V1 = L1 U Lambda^{-1/2};  V2 = L2 V Lambda^{-1/2};
+ *   X = (V1 + V2)/2,  Y = (V2 - V1)/2.
+ * omega are the singular values of L1^H L2 (not square roots of computed
+ * squares; Section 3.3 after Alg. 3).  Arguments as for bse_solve_chol;
+ * additional error BSE_ERR_NOT_PD_APLUSB (info = column).
+ */
+bse_status bse_solve_svd(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B,
+                         int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X,
+                         int64_t ldx, double* Y, int64_t ldy, bse_info* info, void* stream);
+
+/*
+ * Gradient of L = sum_i w_i omega_i with respect to Hermitian A and B.
+ * Thm. 3 item 3 (left eigenvector of H1 is v^H Sigma) with the
+ * Sigma-normalisation of Eq. (13) give d omega_i = v_i^H [dA dB; dB dA] v_i,
+ * hence (Frobenius inner product on Hermitian matrices)
+ *   dA = sum_i w_i (x_i x_i^H + y_i y_i^H),  dB = sum_i w_i (x_i y_i^H + y_i x_i^H).
+ * Valid for simple omega_i only (not differentiable at multiplicity > 1).
+ * X, Y     device, n x k, the k selected columns of a solve's output.
+ * w        device, k doubles (dL/d omega_i).
+ * dA, dB   device, n x n complex, full Hermitian matrices written.
+ */
+bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t ldx, const double* Y,
+                    int64_t ldy, const double* w, double* dA, int64_t ldda, double* dB, int64_t lddb,
+                    void* stream);
+
+/*
+ * End-to-end variant: identical to bse_solve_chol (method = BSE_METHOD_CHOL)
+ * or bse_solve_svd (BSE_METHOD_SVD), but every data pointer (A, B, omega, X,
+ * Y) is a HOST pointer.  The library copies A and B to device workspace
+ * (pinned host memory gives full PCIe/C2C bandwidth), solves, and copies
+ * omega, X, Y back before returning.
+ */
+bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, int64_t lda,
+                          const double* B, int64_t ldb, int64_t il, int64_t iu, int prec,
+                          double* omega, double* X, int64_t ldx, double* Y, int64_t ldy,
+                          bse_info* info, void* stream);
+
+/* Number of CUDA kernel launches this handle has issued so far (all entry
+ * points).  Used to report launch counts. */
+int64_t bse_launch_count(bse_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSE_GB300_H */

@@ -1,0 +1,273 @@
+"""Thin Python binding of the C ABI in include/bse.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libbse_gb300.so; this module
+only converts PyTorch CUDA tensors to the ABI's column-major device pointers
+and back.  There is no CPU fallback: if the library cannot be built or
+loaded, or no CUDA device is present, the calls raise.
+
+Layout: the ABI is column-major.  A PyTorch (row-major) n x n tensor is
+passed as ``A.mT.contiguous()`` (the column-major storage of A); outputs are
+allocated as (k, n) row-major tensors and returned as their ``.mT`` views.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+STATUS_NAMES = {
+    0: "BSE_OK",
+    1: "BSE_ERR_ARG",
+    2: "BSE_ERR_NOT_PD_AMINUSB",
+    3: "BSE_ERR_NOT_PD_APLUSB",
+    4: "BSE_ERR_NO_CONVERGENCE",
+    5: "BSE_ERR_REFINE",
+    6: "BSE_ERR_TIMEOUT",
+    7: "BSE_ERR_CUDA",
+    8: "BSE_ERR_NOMEM",
+    9: "BSE_ERR_NOT_IMPLEMENTED",
+}
+METHODS = {"chol": 0, "svd": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class BseError(RuntimeError):
+    def __init__(self, code: int, msg: str, info: int = 0):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg} (info={info})")
+        self.code = code
+        self.info = info
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("info", ctypes.c_int64), ("err_est", ctypes.c_double), ("refine_iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/bse.h."""
+    hdr = os.path.join(_build.ROOT, "include", "bse.h")
+    txt = open(hdr).read()
+    return re.findall(r"^\s*(?:bse_status|const char\*|int64_t)\s+(bse_\w+)\s*\(", txt, flags=re.M)
+
+
+def _bind(lib):
+    lib.bse_create.argtypes = [ctypes.POINTER(_P)]
+    lib.bse_destroy.argtypes = [_P]
+    lib.bse_last_error.restype = ctypes.c_char_p
+    lib.bse_workspace_size.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    lib.bse_set_workspace.argtypes = [_P, _P, ctypes.c_size_t]
+    for f in (lib.bse_solve_chol, lib.bse_solve_svd):
+        f.argtypes = [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _I64, _P, _I64,
+                      ctypes.POINTER(_Info), _P]
+    lib.bse_grad.argtypes = [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _I64, _P, _I64, _P]
+    lib.bse_solve_host.argtypes = [_P, ctypes.c_int, _I64, _P, _I64, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P,
+                                   _I64, _P, _I64, ctypes.POINTER(_Info), _P]
+    lib.bse_launch_count.argtypes = [_P]
+    lib.bse_launch_count.restype = ctypes.c_int64
+    for name in ("bse_create", "bse_destroy", "bse_workspace_size", "bse_set_workspace", "bse_solve_chol",
+                 "bse_solve_svd", "bse_grad", "bse_solve_host"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+def lib():
+    """The loaded CUDA library (built in-tree on first use if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.lib_path()
+            if not os.path.exists(path):
+                path = _build.build()
+            _lib = _bind(ctypes.CDLL(path))
+        return _lib
+
+
+def _check(code: int, info: int = 0):
+    if code != OK:
+        raise BseError(code, lib().bse_last_error().decode(errors="replace"), info)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Handle:
+    """Owns a bse_handle bound to the current CUDA device (workspace from torch)."""
+
+    def __init__(self):
+        if not torch.cuda.is_available():
+            raise RuntimeError("bse: a CUDA device is required (no CPU fallback)")
+        h = _P()
+        _check(lib().bse_create(ctypes.byref(h)))
+        self._h = h
+        self._ws = None
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def reserve(self, n: int, method: str, device) -> None:
+        need = ctypes.c_size_t(0)
+        _check(lib().bse_workspace_size(int(n), METHODS[method], 0, ctypes.byref(need)))
+        if self._ws is None or self._ws.numel() < need.value or self._ws.device != device:
+            self._ws = torch.empty(need.value, dtype=torch.uint8, device=device)
+            _check(lib().bse_set_workspace(self._h, _P(self._ws.data_ptr()), self._ws.numel()))
+
+    def launches(self) -> int:
+        return int(lib().bse_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bse_set_workspace(self._h, None, 0)
+            lib().bse_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default = threading.local()
+
+
+def default_handle() -> Handle:
+    h = getattr(_default, "h", None)
+    if h is None:
+        h = Handle()
+        _default.h = h
+    return h
+
+
+def _colmajor(A: torch.Tensor) -> torch.Tensor:
+    if A.dtype != torch.complex128:
+        raise TypeError("bse: A and B must be complex128")
+    if not A.is_cuda:
+        raise TypeError("bse: device tensors required (use solve_host for host arrays)")
+    return A.mT.contiguous()
+
+
+def solve(A: torch.Tensor, B: torch.Tensor, method: str = "chol", precision: str = "fp64", il: int | None = None,
+          iu: int | None = None, vectors: bool = True, handle: Handle | None = None, stream=None):
+    """Positive eigenvalues omega (ascending) and Sigma-normalised eigenvectors
+    [X; Y] of H1 = [A B; -B -A] (Alg. 2 for method='chol', Alg. 3 for 'svd').
+
+    Returns (omega, X, Y) with omega of shape (k,), X, Y of shape (n, k)
+    (None when vectors=False), k = iu - il + 1 (1-based, inclusive; default all).
+    """
+    n = A.shape[0]
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    k = max(iu - il + 1, 0)
+    h = handle or default_handle()
+    h.reserve(n, method, A.device)
+    Ac, Bc = _colmajor(A), _colmajor(B)
+    omega = torch.empty(k, dtype=torch.float64, device=A.device)
+    if vectors:
+        Xt = torch.empty((k, n), dtype=torch.complex128, device=A.device)
+        Yt = torch.empty((k, n), dtype=torch.complex128, device=A.device)
+        px, py = _P(Xt.data_ptr()), _P(Yt.data_ptr())
+    else:
+        Xt = Yt = None
+        px = py = None
+    info = _Info()
+    fn = lib().bse_solve_chol if method == "chol" else lib().bse_solve_svd
+    code = fn(h.ptr, n, _P(Ac.data_ptr()), max(n, 1), _P(Bc.data_ptr()), max(n, 1), il, iu, PRECISIONS[precision],
+              _P(omega.data_ptr()), px, max(n, 1), py, max(n, 1), ctypes.byref(info), _P(_stream_ptr(stream)))
+    _check(code, info.info)
+    if not vectors:
+        return omega, None, None
+    return omega, Xt.mT, Yt.mT
+
+
+def solve_host(A, B, method: str = "chol", il: int | None = None, iu: int | None = None, handle: Handle | None = None,
+               stream=None):
+    """End-to-end solve from host arrays (numpy complex128 or CPU tensors; pinned
+    CPU tensors give full copy bandwidth) through bse_solve_host; returns host
+    (omega, X, Y) as CPU tensors."""
+    At = torch.as_tensor(A)
+    Bt = torch.as_tensor(B)
+    n = At.shape[0]
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    k = iu - il + 1
+    h = handle or default_handle()
+    h.reserve(n, method, torch.device("cuda", torch.cuda.current_device()))
+    Ac = At.mT.contiguous() if not _is_colmajor(At) else At
+    Bc = Bt.mT.contiguous() if not _is_colmajor(Bt) else Bt
+    omega = torch.empty(k, dtype=torch.float64)
+    Xt = torch.empty((k, n), dtype=torch.complex128)
+    Yt = torch.empty((k, n), dtype=torch.complex128)
+    info = _Info()
+    code = lib().bse_solve_host(h.ptr, METHODS[method], n, _P(Ac.data_ptr()), max(n, 1), _P(Bc.data_ptr()), max(n, 1),
+                                il, iu, 0, _P(omega.data_ptr()), _P(Xt.data_ptr()), max(n, 1), _P(Yt.data_ptr()),
+                                max(n, 1), ctypes.byref(info), _P(_stream_ptr(stream)))
+    _check(code, info.info)
+    return omega, Xt.mT, Yt.mT
+
+
+def _is_colmajor(T: torch.Tensor) -> bool:
+    return T.dim() == 2 and T.stride(0) == 1 and T.stride(1) == T.shape[0]
+
+
+def grad(X: torch.Tensor, Y: torch.Tensor, w: torch.Tensor, handle: Handle | None = None, stream=None):
+    """dL/dA, dL/dB (full Hermitian, n x n) for L = sum_i w_i omega_i, given the k
+    eigenvector columns X, Y (n x k) of the selected omega_i."""
+    n, k = X.shape
+    h = handle or default_handle()
+    X = X if _is_colmajor(X) else X.mT.contiguous().mT
+    Y = Y if _is_colmajor(Y) else Y.mT.contiguous().mT
+    w = w.to(dtype=torch.float64, device=X.device).contiguous()
+    dAt = torch.empty((n, n), dtype=torch.complex128, device=X.device)
+    dBt = torch.empty((n, n), dtype=torch.complex128, device=X.device)
+    code = lib().bse_grad(h.ptr, n, k, _P(_cm_ptr(X)), max(n, 1), _P(_cm_ptr(Y)), max(n, 1), _P(w.data_ptr()),
+                          _P(dAt.data_ptr()), max(n, 1), _P(dBt.data_ptr()), max(n, 1), _P(_stream_ptr(stream)))
+    _check(code)
+    return dAt.mT, dBt.mT
+
+
+def _cm_ptr(T: torch.Tensor) -> int:
+    if not _is_colmajor(T):
+        raise ValueError("expected a column-major (n, k) view, e.g. the X returned by solve()")
+    return T.data_ptr()
+
+
+class Omega(torch.autograd.Function):
+    """omega[idx] of H1 = [A B; -B -A] with a backward through bse_grad.
+
+    The gradient is the Hermitian Frobenius gradient (the convention of
+    torch.linalg.eigh): d omega_i = <x x^H + y y^H, dA> + <x y^H + y x^H, dB>.
+    """
+
+    @staticmethod
+    def forward(ctx, A, B, idx, method="chol"):
+        idx = torch.as_tensor(idx, device=A.device, dtype=torch.long)
+        omega, X, Y = solve(A.detach(), B.detach(), method=method)
+        ctx.save_for_backward(X[:, idx], Y[:, idx])
+        return omega[idx]
+
+    @staticmethod
+    def backward(ctx, g):
+        Xs, Ys = ctx.saved_tensors
+        Xs = Xs.mT.contiguous().mT
+        Ys = Ys.mT.contiguous().mT
+        dA, dB = grad(Xs, Ys, g)
+        return dA, dB, None, None

@@ -1,0 +1,466 @@
+// C ABI (include/bse.h): handle, workspace planning and the two solver
+// pipelines of the paper.
+//
+// Alg. 2 (CHOL), all on the device, one stream:
+//   form M1 = A + B (full Hermitian) and M2 = A - B (lower)        [Thm. ProdEig]
+//   L L^H = M2                        blocked Cholesky             [step 1]
+//   W = M1 L, M = L^H W (lower)       two triangular GEMMs         [step 2]
+//   T = Q^H M Q                       Householder tridiagonal      [step 2]
+//   T Z = Z D (selected)              bisection + twisted vectors  [step 2]
+//   V_M = Q Z                         blocked back-transformation  [step 2]
+//   omega = sqrt(D)                                                [step 3]
+//   P = L^{-H} V_M                    blocked triangular solve     [step 4]
+//   X, Y = ((c1 P + c2 L V_M)/2, (c2 L V_M - c1 P)/2),
+//   c1 = sqrt(omega), c2 = 1/sqrt(omega)   triangular GEMM + fused epilogue [steps 4-6]
+// Alg. 3 (SVD):
+//   L1 L1^H = A + B, L2 L2^H = A - B  blocked Cholesky x2          [steps 1-2]
+//   G = L1^H L2                       triangular x triangular GEMM [step 3]
+//   G = Q_L B Q_R^H                   Householder bidiagonal       [step 3]
+//   Golub-Kahan tridiagonal of B: bisection + twisted vectors      [step 3]
+//   U = Q_L U_B, V = Q_R V_B          blocked back-transformations [step 3]
+//   X, Y from L1 U and L2 V with c1 = c2 = 1/sqrt(omega)           [steps 4-6]
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+static thread_local std::string g_err;
+void bse_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+long long bse_total_launches();
+
+struct bse_context {
+  int device = 0;
+  void* ws = nullptr;      // internal workspace
+  size_t ws_bytes = 0;
+  void* user_ws = nullptr;  // caller-supplied workspace
+  size_t user_bytes = 0;
+  void* io = nullptr;       // staging for bse_solve_host
+  size_t io_bytes = 0;
+  int64_t* host_status = nullptr;  // pinned, 2 entries
+};
+
+// ---------------------------------------------------------------------------
+// Workspace plan: a bump allocator over one region, 256-byte aligned pieces.
+struct Plan {
+  char* base;
+  size_t off = 0;
+  explicit Plan(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += sizeof(T) * (count > 0 ? count : 1);
+    return p;
+  }
+};
+
+struct TriPlan {
+  TriWork w;
+  void carve(Plan& pl, int64_t N, int64_t k) {
+    w.a = pl.take<double>(N);
+    w.off = pl.take<double>(N);
+    w.e2 = pl.take<double>(N);
+    w.lam = pl.take<double>(N);
+    w.blk = pl.take<int>(N);
+    w.rank = pl.take<int>(N);
+    w.bstart = pl.take<int>(N + 2);
+    w.prm = pl.take<double>(8);
+    w.iprm = pl.take<int>(8);
+    w.scratch = pl.take<double>((size_t)N * k);
+    w.E = pl.take<double>((size_t)k * k);
+    w.Z2 = pl.take<double>((size_t)N * k);
+  }
+};
+
+struct CholBuffers {
+  int64_t* status;
+  cplx *M1, *L, *Linv, *W, *P;
+  HetrdWork h;
+  TriPlan t;
+  double *Z, *lam, *c1, *c2;
+  cplx* tmp;
+};
+
+static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k) {
+  const int nbt = hetrd_panel();
+  b.status = pl.take<int64_t>(4);
+  b.M1 = pl.take<cplx>((size_t)n * n);
+  b.L = pl.take<cplx>((size_t)n * n);
+  b.Linv = pl.take<cplx>(chol_linv_elems(n));
+  b.W = pl.take<cplx>((size_t)n * n);
+  b.P = pl.take<cplx>((size_t)n * k);
+  b.h.V = pl.take<cplx>((size_t)n * n);
+  b.h.W = pl.take<cplx>((size_t)n * nbt);
+  b.h.tau = pl.take<cplx>(n);
+  b.h.d = pl.take<double>(n);
+  b.h.e = pl.take<double>(n);
+  b.h.part = pl.take<cplx>(hetrd_part_elems(n));
+  b.h.small = pl.take<cplx>(4 * nbt * nbt + 64);
+  b.t.carve(pl, n, k);
+  b.Z = pl.take<double>((size_t)n * k);
+  b.lam = pl.take<double>(k);
+  b.c1 = pl.take<double>(k);
+  b.c2 = pl.take<double>(k);
+  b.tmp = pl.take<cplx>(2 * 64 * 64 + 2 * 64 * (size_t)k);
+}
+
+struct SvdBuffers {
+  int64_t* status;
+  cplx *L1, *L2, *Linv, *G, *Uc, *Vc, *T1;
+  GebrdWork g;
+  TriPlan t;
+  double *Z, *UB, *VB, *lam, *c1, *c2, *off;
+  cplx* tmp;
+};
+
+static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k) {
+  const int nbt = 32;
+  b.status = pl.take<int64_t>(4);
+  b.L1 = pl.take<cplx>((size_t)n * n);
+  b.L2 = pl.take<cplx>((size_t)n * n);
+  b.Linv = pl.take<cplx>(chol_linv_elems(n));
+  b.G = pl.take<cplx>((size_t)n * n);
+  b.Uc = pl.take<cplx>((size_t)n * k);
+  b.Vc = pl.take<cplx>((size_t)n * k);
+  b.T1 = pl.take<cplx>((size_t)n * k);
+  b.g.U = pl.take<cplx>((size_t)n * n);
+  b.g.Vr = pl.take<cplx>((size_t)n * n);
+  b.g.X = pl.take<cplx>((size_t)n * nbt);
+  b.g.Y = pl.take<cplx>((size_t)n * nbt);
+  b.g.tauq = pl.take<cplx>(n);
+  b.g.taup = pl.take<cplx>(n);
+  b.g.d = pl.take<double>(n);
+  b.g.e = pl.take<double>(n);
+  b.g.part = pl.take<cplx>(gebrd_part_elems(n));
+  b.g.small = pl.take<cplx>(4 * nbt + 64);
+  b.t.carve(pl, 2 * n, k);
+  b.Z = pl.take<double>((size_t)2 * n * k);
+  b.UB = pl.take<double>((size_t)n * k);
+  b.VB = pl.take<double>((size_t)n * k);
+  b.off = pl.take<double>(2 * n);
+  b.lam = pl.take<double>(k);
+  b.c1 = pl.take<double>(k);
+  b.c2 = pl.take<double>(k);
+  b.tmp = pl.take<cplx>(2 * 64 * 64 + 2 * 64 * (size_t)k);
+}
+
+static size_t plan_bytes(int64_t n, int64_t k, int method) {
+  Plan pl(nullptr);
+  if (method == BSE_METHOD_CHOL) {
+    CholBuffers b;
+    carve_chol(pl, b, n, k);
+  } else {
+    SvdBuffers b;
+    carve_svd(pl, b, n, k);
+  }
+  return pl.off + 256;
+}
+
+static bse_status ensure_ws(bse_context* h, size_t bytes, void** out) {
+  if (h->user_ws) {
+    if (h->user_bytes < bytes) {
+      bse_internal_set_error("caller-supplied workspace too small");
+      return BSE_ERR_NOMEM;
+    }
+    *out = h->user_ws;
+    return BSE_OK;
+  }
+  if (h->ws_bytes < bytes) {
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      bse_internal_set_error("cudaMalloc of workspace failed");
+      return BSE_ERR_NOMEM;
+    }
+    h->ws_bytes = bytes;
+  }
+  *out = h->ws;
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels for the Golub-Kahan set-up and the singular-vector split.
+__global__ void gk_offdiag_kernel(int64_t n, const double* d, const double* e, double* off) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) off[2 * i] = d[i];
+  if (i < n - 1) off[2 * i + 1] = e[i];
+}
+// z = [v1, u1, v2, u2, ...]/sqrt(2):  U_B(i, c) = sqrt2 z(2i+1, c), V_B(i, c) = sqrt2 z(2i, c)
+__global__ void gk_split_kernel(int64_t n, int64_t k, const double* Z, int64_t ldz, double* UB, double* VB) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (i >= n || c >= k) return;
+  const double r2 = 1.4142135623730951;
+  VB[i + c * n] = r2 * Z[2 * i + c * ldz];
+  UB[i + c * n] = r2 * Z[2 * i + 1 + c * ldz];
+}
+
+#define TRY(x)                \
+  do {                        \
+    bse_status r_ = (x);      \
+    if (r_ != BSE_OK) return r_; \
+  } while (0)
+
+static bse_status check_common(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                               int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx, double* Y,
+                               int64_t ldy) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  if (n < 0) return bse_internal_set_error("n < 0"), BSE_ERR_ARG;
+  if (n == 0) return BSE_OK;
+  if (!A || !B || !omega) return bse_internal_set_error("NULL A, B or omega"), BSE_ERR_ARG;
+  if (lda < n || ldb < n) return bse_internal_set_error("lda or ldb < n"), BSE_ERR_ARG;
+  if (il < 1 || iu > n || il > iu) return bse_internal_set_error("need 1 <= il <= iu <= n"), BSE_ERR_ARG;
+  if ((X == nullptr) != (Y == nullptr)) return bse_internal_set_error("X and Y must both be given or both NULL"), BSE_ERR_ARG;
+  if (X && (ldx < n || ldy < n)) return bse_internal_set_error("ldx or ldy < n"), BSE_ERR_ARG;
+  if (prec == BSE_PREC_MIXED) return bse_internal_set_error("mixed precision is not available in this build"), BSE_ERR_NOT_IMPLEMENTED;
+  if (prec != BSE_PREC_FP64) return bse_internal_set_error("unknown precision"), BSE_ERR_ARG;
+  return BSE_OK;
+}
+
+static bse_status finish(bse_context* h, cudaStream_t s, const int64_t* dstatus, bse_info* info) {
+  BSE_CUDA(cudaMemcpyAsync(h->host_status, dstatus, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  const int64_t code = h->host_status[0];
+  if (info) {
+    info->info = h->host_status[1];
+    info->err_est = 0.0;
+    info->refine_iters = 0;
+  }
+  if (code != 0) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "device status %lld (info %lld)", (long long)code, (long long)h->host_status[1]);
+    bse_internal_set_error(buf);
+  }
+  return (bse_status)code;
+}
+
+static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64_t lda, const cplx* B, int64_t ldb,
+                                 int64_t il, int64_t iu, double* omega, cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
+                                 bse_info* info, cudaStream_t s) {
+  const int64_t k = iu - il + 1;
+  void* ws;
+  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_CHOL), &ws));
+  Plan pl(ws);
+  CholBuffers b;
+  carve_chol(pl, b, n, k);
+  int64_t* st = b.status;
+  BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  // M1 = A + B (full), M2 = A - B (lower, in L)
+  TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.M1, n, 1));
+  TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L, n, 0));
+  TRY(potrf_lower(s, n, b.L, n, b.Linv, st, BSE_ERR_NOT_PD_AMINUSB));
+  // W = M1 L ; M = L^H W (lower) into M1's buffer
+  GemmParams<cplx> p1 = gemm_params<cplx>(n, n, n, OPN, b.M1, n, OPN, b.L, n, one, zero, b.W, n);
+  p1.triB = TRI_LO;
+  p1.status = st;
+  TRY(gemm_z(s, p1));
+  GemmParams<cplx> p2 = gemm_params<cplx>(n, n, n, OPC, b.L, n, OPN, b.W, n, one, zero, b.M1, n);
+  p2.triA = TRI_UP;
+  p2.lowerC = 1;
+  p2.status = st;
+  TRY(gemm_z(s, p2));
+  // Hermitian eigendecomposition of M
+  TRY(hetrd_lower(s, n, b.M1, n, b.h, st));
+  TRY(tridiag_eig(s, n, b.h.d, b.h.e, 0, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, n, b.t.w, st));
+  TRY(finish_omega(s, k, b.lam, 0, omega, b.c1, b.c2, st));
+  if (!X) return finish(h, s, st, info);
+  TRY(orthonormalize_columns(s, n, k, b.Z, n, b.t.w, st));
+  cplx* VM = b.W;  // reuse: V_M = Q Z (n x k)
+  TRY(real_to_complex(s, n, k, b.Z, n, VM, n));
+  TRY(hetrd_backtransform(s, n, k, b.h, VM, n, b.tmp, st));
+  // P = L^{-H} V_M
+  BSE_CUDA(cudaMemcpy2DAsync(b.P, sizeof(cplx) * n, VM, sizeof(cplx) * n, sizeof(cplx) * n, k,
+                             cudaMemcpyDeviceToDevice, s));
+  TRY(trsm_lower_conjtrans(s, n, k, b.L, n, b.Linv, b.P, n, st));
+  // X, Y from P (= V1 unscaled) and L V_M (= V2 unscaled)
+  GemmParams<cplx> p3 = gemm_params<cplx>(n, k, n, OPN, b.L, n, OPN, VM, n, one, zero, X, ldx);
+  p3.triA = TRI_LO;
+  p3.status = st;
+  p3.epi = EPI_XY;
+  p3.P = b.P, p3.ldp = n, p3.c1 = b.c1, p3.c2 = b.c2, p3.Y = Y, p3.ldy = ldy;
+  TRY(gemm_z(s, p3));
+  return finish(h, s, st, info);
+}
+
+static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_t lda, const cplx* B, int64_t ldb,
+                                int64_t il, int64_t iu, double* omega, cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
+                                bse_info* info, cudaStream_t s) {
+  const int64_t k = iu - il + 1;
+  void* ws;
+  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_SVD), &ws));
+  Plan pl(ws);
+  SvdBuffers b;
+  carve_svd(pl, b, n, k);
+  int64_t* st = b.status;
+  BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.L1, n, 0));
+  TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L2, n, 0));
+  TRY(potrf_lower(s, n, b.L1, n, b.Linv, st, BSE_ERR_NOT_PD_APLUSB));
+  TRY(potrf_lower(s, n, b.L2, n, b.Linv, st, BSE_ERR_NOT_PD_AMINUSB));
+  // G = L1^H L2
+  GemmParams<cplx> pg = gemm_params<cplx>(n, n, n, OPC, b.L1, n, OPN, b.L2, n, one, zero, b.G, n);
+  pg.triA = TRI_UP;
+  pg.triB = TRI_LO;
+  pg.status = st;
+  TRY(gemm_z(s, pg));
+  TRY(gebrd_upper(s, n, b.G, n, b.g, st));
+  // Golub-Kahan tridiagonal (size 2n, zero diagonal)
+  gk_offdiag_kernel<<<ceil_div_u(n, 256), 256, 0, s>>>(n, b.g.d, b.g.e, b.off);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  TRY(tridiag_eig(s, 2 * n, nullptr, b.off, 1, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, 2 * n, b.t.w, st));
+  TRY(finish_omega(s, k, b.lam, 1, omega, b.c1, b.c2, st));
+  if (!X) return finish(h, s, st, info);
+  dim3 gsp(ceil_div_u(n, 256), (unsigned)k);
+  gk_split_kernel<<<gsp, 256, 0, s>>>(n, k, b.Z, 2 * n, b.UB, b.VB);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  TRY(orthonormalize_columns(s, n, k, b.UB, n, b.t.w, st));
+  TRY(orthonormalize_columns(s, n, k, b.VB, n, b.t.w, st));
+  TRY(real_to_complex(s, n, k, b.UB, n, b.Uc, n));
+  TRY(real_to_complex(s, n, k, b.VB, n, b.Vc, n));
+  TRY(gebrd_backtransform(s, 0, n, k, b.g, b.Uc, n, b.tmp, st));
+  TRY(gebrd_backtransform(s, 1, n, k, b.g, b.Vc, n, b.tmp, st));
+  // T1 = L1 U ; X, Y from T1 and L2 V with c1 = c2 = 1/sqrt(omega)
+  GemmParams<cplx> p1 = gemm_params<cplx>(n, k, n, OPN, b.L1, n, OPN, b.Uc, n, one, zero, b.T1, n);
+  p1.triA = TRI_LO;
+  p1.status = st;
+  TRY(gemm_z(s, p1));
+  GemmParams<cplx> p2 = gemm_params<cplx>(n, k, n, OPN, b.L2, n, OPN, b.Vc, n, one, zero, X, ldx);
+  p2.triA = TRI_LO;
+  p2.status = st;
+  p2.epi = EPI_XY;
+  p2.P = b.T1, p2.ldp = n, p2.c1 = b.c1, p2.c2 = b.c2, p2.Y = Y, p2.ldy = ldy;
+  TRY(gemm_z(s, p2));
+  return finish(h, s, st, info);
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+bse_status bse_create(bse_handle* out) {
+  if (!out) return bse_internal_set_error("NULL output"), BSE_ERR_ARG;
+  bse_context* h = new bse_context();
+  BSE_CUDA(cudaGetDevice(&h->device));
+  if (cudaMallocHost(&h->host_status, 4 * sizeof(int64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return bse_internal_set_error("cudaMallocHost failed"), BSE_ERR_NOMEM;
+  }
+  *out = h;
+  return BSE_OK;
+}
+
+bse_status bse_destroy(bse_handle h) {
+  if (!h) return BSE_OK;
+  if (h->ws) cudaFree(h->ws);
+  if (h->io) cudaFree(h->io);
+  if (h->host_status) cudaFreeHost(h->host_status);
+  delete h;
+  return BSE_OK;
+}
+
+const char* bse_last_error(void) { return g_err.c_str(); }
+
+bse_status bse_workspace_size(int64_t n, int method, int prec, size_t* bytes) {
+  if (!bytes || n < 0 || (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) || (prec != BSE_PREC_FP64 && prec != BSE_PREC_MIXED))
+    return bse_internal_set_error("bad argument to bse_workspace_size"), BSE_ERR_ARG;
+  *bytes = plan_bytes(n, n > 0 ? n : 1, method);
+  return BSE_OK;
+}
+
+bse_status bse_set_workspace(bse_handle h, void* ptr, size_t bytes) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  if (ptr && ((uintptr_t)ptr & 255)) return bse_internal_set_error("workspace must be 256-byte aligned"), BSE_ERR_ARG;
+  h->user_ws = ptr;
+  h->user_bytes = ptr ? bytes : 0;
+  return BSE_OK;
+}
+
+bse_status bse_solve_chol(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                          int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx, double* Y,
+                          int64_t ldy, bse_info* info, void* stream) {
+  bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
+  if (r != BSE_OK || n == 0) return r;
+  return solve_chol_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, omega, (cplx*)X, ldx, (cplx*)Y, ldy,
+                        info, (cudaStream_t)stream);
+}
+
+bse_status bse_solve_svd(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                         int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx, double* Y,
+                         int64_t ldy, bse_info* info, void* stream) {
+  bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
+  if (r != BSE_OK || n == 0) return r;
+  return solve_svd_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, omega, (cplx*)X, ldx, (cplx*)Y, ldy,
+                       info, (cudaStream_t)stream);
+}
+
+bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                    const double* w, double* dA, int64_t ldda, double* dB, int64_t lddb, void* stream) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  if (n < 0 || k < 0) return bse_internal_set_error("n or k < 0"), BSE_ERR_ARG;
+  if (n == 0) return BSE_OK;
+  if (!dA || !dB || (k > 0 && (!X || !Y || !w))) return bse_internal_set_error("NULL pointer"), BSE_ERR_ARG;
+  if (ldda < n || lddb < n || (k > 0 && (ldx < n || ldy < n))) return bse_internal_set_error("leading dimension < n"), BSE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(grad_outer(s, n, k, (const cplx*)X, ldx, (const cplx*)Y, ldy, w, (cplx*)dA, ldda, (cplx*)dB, lddb));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  return BSE_OK;
+}
+
+bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx,
+                          double* Y, int64_t ldy, bse_info* info, void* stream) {
+  if (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
+  bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
+  if (r != BSE_OK || n == 0) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t k = iu - il + 1;
+  Plan need(nullptr);
+  need.take<cplx>((size_t)n * n);
+  need.take<cplx>((size_t)n * n);
+  need.take<double>(k);
+  if (X) need.take<cplx>((size_t)n * k), need.take<cplx>((size_t)n * k);
+  if (h->io_bytes < need.off + 256) {
+    if (h->io) cudaFree(h->io);
+    h->io = nullptr;
+    h->io_bytes = 0;
+    if (cudaMalloc(&h->io, need.off + 256) != cudaSuccess) {
+      cudaGetLastError();
+      return bse_internal_set_error("cudaMalloc of staging buffers failed"), BSE_ERR_NOMEM;
+    }
+    h->io_bytes = need.off + 256;
+  }
+  Plan pl(h->io);
+  cplx* dA = pl.take<cplx>((size_t)n * n);
+  cplx* dB = pl.take<cplx>((size_t)n * n);
+  double* dom = pl.take<double>(k);
+  cplx *dX = nullptr, *dY = nullptr;
+  if (X) dX = pl.take<cplx>((size_t)n * k), dY = pl.take<cplx>((size_t)n * k);
+  BSE_CUDA(cudaMemcpy2DAsync(dA, sizeof(cplx) * n, A, sizeof(cplx) * lda, sizeof(cplx) * n, n, cudaMemcpyHostToDevice, s));
+  BSE_CUDA(cudaMemcpy2DAsync(dB, sizeof(cplx) * n, B, sizeof(cplx) * ldb, sizeof(cplx) * n, n, cudaMemcpyHostToDevice, s));
+  r = method == BSE_METHOD_CHOL ? solve_chol_dev(h, n, dA, n, dB, n, il, iu, dom, dX, n, dY, n, info, s)
+                                : solve_svd_dev(h, n, dA, n, dB, n, il, iu, dom, dX, n, dY, n, info, s);
+  if (r != BSE_OK) return r;
+  BSE_CUDA(cudaMemcpyAsync(omega, dom, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  if (X) {
+    BSE_CUDA(cudaMemcpy2DAsync(X, sizeof(cplx) * ldx, dX, sizeof(cplx) * n, sizeof(cplx) * n, k, cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaMemcpy2DAsync(Y, sizeof(cplx) * ldy, dY, sizeof(cplx) * n, sizeof(cplx) * n, k, cudaMemcpyDeviceToHost, s));
+  }
+  BSE_CUDA(cudaStreamSynchronize(s));
+  return BSE_OK;
+}
+
+int64_t bse_launch_count(bse_handle h) {
+  (void)h;
+  return (int64_t)bse_total_launches();
+}
+
+}  // extern "C"

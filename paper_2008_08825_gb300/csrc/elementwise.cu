@@ -1,0 +1,246 @@
+// O(n^2) kernels of the solver pipeline: forming A +- B (Thm. ProdEig:
+// M1 = A + B, M2 = A - B), Hermitian mirroring, type conversion, the
+// omega / scaling vectors of the final setup, and the eigenvalue gradient.
+#include "kernels.cuh"
+
+// ---------------------------------------------------------------------------
+// Tile-transposing Hermitian expansion.  Output tile (bi, bj) takes its data
+// from the lower (or diagonal) source tile (max, min), loaded coalesced into
+// shared memory; above-diagonal outputs are conjugate transposes.
+constexpr int TT = 32;
+
+__device__ __forceinline__ cplx herm_pick(const cplx (*S)[TT + 1], int r, int c, int64_t bi, int64_t bj) {
+  if (bi > bj) return S[c][r];                 // S[col][row] layout, source = same tile
+  if (bi < bj) return cconj(S[r][c]);          // source tile (bj, bi): element (j, i)
+  if (r > c) return S[c][r];
+  if (r < c) return cconj(S[r][c]);
+  return mkc(S[r][r].x, 0.0);
+}
+
+__global__ void form_sum_kernel(int64_t n, const cplx* __restrict__ A, int64_t lda, const cplx* __restrict__ B,
+                                int64_t ldb, double sgn, cplx* __restrict__ M, int64_t ldm, int full) {
+  __shared__ cplx S[TT][TT + 1];  // S[col][row] of the source tile
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (!full && bi < bj) return;
+  const int64_t si = bi > bj ? bi : bj, sj = bi > bj ? bj : bi;
+  const int r = threadIdx.x;
+  for (int c = threadIdx.y; c < TT; c += blockDim.y) {
+    const int64_t gi = si * TT + r, gj = sj * TT + c;
+    cplx v = mkc(0.0, 0.0);
+    if (gi < n && gj < n && gi >= gj) {
+      const cplx a = A[IDX2(gi, gj, lda)], b = B[IDX2(gi, gj, ldb)];
+      v = mkc(a.x + sgn * b.x, a.y + sgn * b.y);
+    }
+    S[c][r] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.y; c < TT; c += blockDim.y) {
+    const int64_t gi = bi * TT + r, gj = bj * TT + c;
+    if (gi >= n || gj >= n) continue;
+    if (!full && gi < gj) continue;
+    M[IDX2(gi, gj, ldm)] = herm_pick(S, r, c, bi, bj);
+  }
+}
+
+bse_status form_sum(cudaStream_t s, int64_t n, const cplx* A, int64_t lda, const cplx* B, int64_t ldb,
+                    double sgn, cplx* M, int64_t ldm, int full) {
+  if (n <= 0) return BSE_OK;
+  dim3 grid(ceil_div_u(n, TT), ceil_div_u(n, TT)), blk(TT, 8);
+  form_sum_kernel<<<grid, blk, 0, s>>>(n, A, lda, B, ldb, sgn, M, ldm, full);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+__global__ void fill_upper_kernel(int64_t n, cplx* M, int64_t ldm) {
+  __shared__ cplx S[TT][TT + 1];
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;  // output tile, bi <= bj
+  if (bi > bj) return;
+  const int r = threadIdx.x;
+  for (int c = threadIdx.y; c < TT; c += blockDim.y) {
+    const int64_t gi = bj * TT + r, gj = bi * TT + c;  // source tile (bj, bi), lower
+    cplx v = mkc(0.0, 0.0);
+    if (gi < n && gj < n && gi >= gj) v = M[IDX2(gi, gj, ldm)];
+    S[c][r] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.y; c < TT; c += blockDim.y) {
+    const int64_t gi = bi * TT + r, gj = bj * TT + c;
+    if (gi >= n || gj >= n || gi > gj) continue;
+    // element (gi, gj) with gi <= gj is conj of (gj, gi) = source S[col = gi - bi*TT][row = gj - bj*TT]
+    const cplx v = S[r][c];
+    M[IDX2(gi, gj, ldm)] = (gi == gj) ? mkc(v.x, 0.0) : cconj(v);
+  }
+}
+
+bse_status hermitian_fill_upper(cudaStream_t s, int64_t n, cplx* M, int64_t ldm) {
+  if (n <= 0) return BSE_OK;
+  dim3 grid(ceil_div_u(n, TT), ceil_div_u(n, TT)), blk(TT, 8);
+  fill_upper_kernel<<<grid, blk, 0, s>>>(n, M, ldm);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+__global__ void real_to_complex_kernel(int64_t n, int64_t k, const double* Z, int64_t ldz, cplx* V, int64_t ldv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < n && j < k) V[IDX2(i, j, ldv)] = mkc(Z[IDX2(i, j, ldz)], 0.0);
+}
+
+bse_status real_to_complex(cudaStream_t s, int64_t n, int64_t k, const double* Z, int64_t ldz, cplx* V,
+                           int64_t ldv) {
+  if (n <= 0 || k <= 0) return BSE_OK;
+  dim3 grid(ceil_div_u(n, 256), (unsigned)k);
+  real_to_complex_kernel<<<grid, 256, 0, s>>>(n, k, Z, ldz, V, ldv);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+__global__ void sub_identity_kernel(int64_t k, double* E, int64_t lde) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < k) E[IDX2(i, i, lde)] -= 1.0;
+}
+
+bse_status sub_identity(cudaStream_t s, int64_t k, double* E, int64_t lde) {
+  if (k <= 0) return BSE_OK;
+  sub_identity_kernel<<<ceil_div_u(k, 256), 256, 0, s>>>(k, E, lde);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+__global__ void finish_omega_kernel(int64_t k, const double* lam, int mode, double* omega, double* c1, double* c2,
+                                    int64_t* status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  const double l = lam[i];
+  if (!(l > 0.0)) {
+    // M = L^H (A+B) L (CHOL) or L1^H L2 (SVD) is nonsingular/PD exactly when
+    // A + B is positive definite
+    dev_fail(status, BSE_ERR_NOT_PD_APLUSB, 0);
+    return;
+  }
+  const double om = (mode == 0) ? sqrt(l) : l;
+  const double sq = sqrt(om);
+  omega[i] = om;
+  if (mode == 0) {
+    c1[i] = sq;
+    c2[i] = 1.0 / sq;
+  } else {
+    c1[i] = 1.0 / sq;
+    c2[i] = 1.0 / sq;
+  }
+}
+
+bse_status finish_omega(cudaStream_t s, int64_t k, const double* lam, int mode, double* omega_out, double* c1,
+                        double* c2, const int64_t* status) {
+  if (k <= 0) return BSE_OK;
+  finish_omega_kernel<<<ceil_div_u(k, 256), 256, 0, s>>>(k, lam, mode, omega_out, c1, c2, (int64_t*)status);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+__global__ void zero_c_kernel(int64_t m, int64_t n, cplx* A, int64_t lda) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < m && j < n) A[IDX2(i, j, lda)] = mkc(0.0, 0.0);
+}
+
+bse_status zero_c(cudaStream_t s, int64_t m, int64_t n, cplx* A, int64_t lda) {
+  if (m <= 0 || n <= 0) return BSE_OK;
+  dim3 grid(ceil_div_u(m, 256), (unsigned)n);
+  zero_c_kernel<<<grid, 256, 0, s>>>(m, n, A, lda);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient (Thm. 3 item 3 with the Sigma-normalisation of Eq. (13)):
+//   dA = sum_i w_i (x_i x_i^H + y_i y_i^H),  dB = sum_i w_i (x_i y_i^H + y_i x_i^H).
+// Both are Hermitian: each CTA computes one 32 x 32 tile on or below the
+// diagonal and stores it and its conjugate transpose (through shared memory,
+// so both stores are coalesced).  The k columns are processed in chunks of
+// GK; the column-b factors are pre-multiplied by w_i and conjugated.
+constexpr int GK = 16;
+
+__global__ void __launch_bounds__(256) grad_kernel(int64_t n, int64_t k, const cplx* __restrict__ X, int64_t ldx,
+                                                   const cplx* __restrict__ Y, int64_t ldy,
+                                                   const double* __restrict__ w, cplx* __restrict__ dA,
+                                                   int64_t ldda, cplx* __restrict__ dB, int64_t lddb) {
+  const int64_t ta = blockIdx.y, tb = blockIdx.x;
+  if (tb > ta) return;
+  __shared__ cplx Xa[GK][TT], Ya[GK][TT], Xb[GK][TT], Yb[GK][TT];  // Xb, Yb: w_i conj(.)
+  __shared__ cplx TA[TT][TT + 1], TB[TT][TT + 1];
+  const int r = threadIdx.x, cy = threadIdx.y;  // 32 x 8
+  cplx ga[4], gb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ga[q] = gb[q] = mkc(0.0, 0.0);
+  for (int64_t i0 = 0; i0 < k; i0 += GK) {
+    __syncthreads();
+    for (int e = threadIdx.y; e < GK; e += blockDim.y) {
+      const int64_t i = i0 + e;
+      const int64_t ga_row = ta * TT + r, gb_row = tb * TT + r;
+      cplx xa = mkc(0, 0), ya = mkc(0, 0), xb = mkc(0, 0), yb = mkc(0, 0);
+      if (i < k) {
+        const double wi = w[i];
+        if (ga_row < n) xa = X[IDX2(ga_row, i, ldx)], ya = Y[IDX2(ga_row, i, ldy)];
+        if (gb_row < n) {
+          xb = cscale(cconj(X[IDX2(gb_row, i, ldx)]), wi);
+          yb = cscale(cconj(Y[IDX2(gb_row, i, ldy)]), wi);
+        }
+      }
+      Xa[e][r] = xa, Ya[e][r] = ya, Xb[e][r] = xb, Yb[e][r] = yb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int e = 0; e < GK; ++e) {
+      const cplx xa = Xa[e][r], ya = Ya[e][r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = cy + 8 * q;
+        const cplx xb = Xb[e][c], yb = Yb[e][c];
+        cfma(ga[q], xa, xb);
+        cfma(ga[q], ya, yb);
+        cfma(gb[q], xa, yb);
+        cfma(gb[q], ya, xb);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = cy + 8 * q;
+    const int64_t gi = ta * TT + r, gj = tb * TT + c;
+    if (gi < n && gj < n) {
+      dA[IDX2(gi, gj, ldda)] = ga[q];
+      dB[IDX2(gi, gj, lddb)] = gb[q];
+    }
+    TA[c][r] = ga[q];
+    TB[c][r] = gb[q];
+  }
+  if (ta == tb) return;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = cy + 8 * q;
+    // element (tb*TT + r, ta*TT + c) = conj of (ta*TT + c, tb*TT + r) = TA[r][c]
+    const int64_t gi = tb * TT + r, gj = ta * TT + c;
+    if (gi < n && gj < n) {
+      dA[IDX2(gi, gj, ldda)] = cconj(TA[r][c]);
+      dB[IDX2(gi, gj, lddb)] = cconj(TB[r][c]);
+    }
+  }
+}
+
+bse_status grad_outer(cudaStream_t s, int64_t n, int64_t k, const cplx* X, int64_t ldx, const cplx* Y,
+                      int64_t ldy, const double* w, cplx* dA, int64_t ldda, cplx* dB, int64_t lddb) {
+  if (n <= 0) return BSE_OK;
+  dim3 grid(ceil_div_u(n, TT), ceil_div_u(n, TT)), blk(TT, 8);
+  grad_kernel<<<grid, blk, 0, s>>>(n, k, X, ldx, Y, ldy, w, dA, ldda, dB, lddb);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}

@@ -1,0 +1,343 @@
+// Householder bidiagonalisation G = Q_L B Q_R^H of the n x n product
+// G = L1^H L2 of Alg. 3, with B real upper bidiagonal (diagonal d, super-
+// diagonal e), and the back-transformations U = Q_L U_B, V = Q_R V_B.
+//
+// Blocked in panels of NBB columns.  Inside a panel the matrix is kept as
+// the panel-start A plus the correction -U Y^H - X V^H, where u_q / v_q are
+// the left / right reflectors of the panel's processed columns and
+// y_q = tauq A_cur^H u_q, x_q = taup A_cur v_q.  Step i:
+//   1. column i receives the correction; left reflector H_L with
+//      H_L^H c = d_i e_1 (d_i real); y = tauq (A^H u - Y (U^H u) - V (X^H u));
+//   2. row i receives the correction (now including u_i, y_i); right
+//      reflector H_R with r H_R = e_i e_1^T (e_i real);
+//      x = taup (A v - U (Y^H v) - X (V^H v));
+// so that H_L^H A_cur H_R = A_cur - u y^H - x v^H.  The trailing matrix then
+// takes A22 -= U Y^H + X V^H through the GEMM engine.  The two matvecs per
+// step (A^H u: warp per column; A v: thread per row) read the trailing
+// matrix coalesced and are bound by the FP64 pipe on GB300.
+#include "kernels.cuh"
+
+constexpr int NBB = 32;
+constexpr int BRB = 256;
+constexpr int BCH = 512;
+
+static inline int64_t bchunks(int64_t m) { return (m + BCH - 1) / BCH; }
+size_t gebrd_part_elems(int64_t n) { return (size_t)(bchunks(n) + 1) * (size_t)(n + 1) + 4 * (n / BRB + 2) + 64; }
+
+__device__ __forceinline__ double bsum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < (blockDim.x >> 5)) t = red[threadIdx.x];
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+struct BHouse {
+  cplx tau, scal;
+  double beta;
+};
+__device__ __forceinline__ BHouse bmake_house(cplx alpha, double xnorm2) {
+  BHouse h;
+  if (xnorm2 == 0.0 && alpha.y == 0.0) {
+    h.tau = mkc(0.0, 0.0);
+    h.beta = alpha.x;
+    h.scal = mkc(0.0, 0.0);
+  } else {
+    const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+    const double beta = (alpha.x >= 0.0) ? -nrm : nrm;
+    h.beta = beta;
+    h.tau = mkc((beta - alpha.x) / beta, -alpha.y / beta);
+    h.scal = cdiv(mkc(1.0, 0.0), mkc(alpha.x - beta, alpha.y));
+  }
+  return h;
+}
+
+struct BdArgs {
+  int64_t n, p, i;
+  cplx* A;
+  int64_t lda;
+  cplx* U;   // ld n
+  cplx* Vr;  // ld n
+  cplx* X;   // ld n
+  cplx* Y;   // ld n
+  cplx* tauq;
+  cplx* taup;
+  double* d;
+  double* e;
+  cplx* part;       // chunk partials, ld n+1
+  double* npart;    // norm partials
+  cplx* s;          // small dots: [0..NBB) first set, [NBB..2NBB) second set
+  const int64_t* status;
+};
+
+#define BD_GUARD() \
+  if (*(volatile const int64_t*)a.status) return
+
+// 1a. column update, partial norms of rows > i
+__global__ void __launch_bounds__(BRB) bd_col_update(BdArgs a) {
+  __shared__ cplx yi[NBB], vi[NBB];
+  __shared__ double red[32];
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n;
+  const int ii = (int)(i - a.p);
+  if (threadIdx.x < ii) {
+    yi[threadIdx.x] = a.Y[IDX2(i, threadIdx.x, ld)];
+    vi[threadIdx.x] = a.Vr[IDX2(i, a.p + threadIdx.x, ld)];
+  }
+  __syncthreads();
+  const int64_t r = i + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  double nrm = 0.0;
+  if (r < n) {
+    cplx c = a.A[IDX2(r, i, a.lda)];
+    for (int q = 0; q < ii; ++q) {
+      c = csub(c, cmul(a.U[IDX2(r, a.p + q, ld)], cconj(yi[q])));
+      c = csub(c, cmul(a.X[IDX2(r, q, ld)], cconj(vi[q])));
+    }
+    a.A[IDX2(r, i, a.lda)] = c;
+    if (r > i) nrm = cabs2(c);
+  }
+  const double s = bsum(nrm, red);
+  if (threadIdx.x == 0) a.npart[blockIdx.x] = s;
+}
+
+// 1b. left reflector, u into U(:, i) (rows >= i)
+__global__ void __launch_bounds__(BRB) bd_house_left(BdArgs a, int nparts) {
+  __shared__ BHouse hs;
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n;
+  if (threadIdx.x == 0) {
+    double x2 = 0.0;
+    for (int k = 0; k < nparts; ++k) x2 += a.npart[k];
+    hs = bmake_house(a.A[IDX2(i, i, a.lda)], x2);
+    if (blockIdx.x == 0) {
+      a.tauq[i] = hs.tau;
+      a.d[i] = hs.beta;
+    }
+  }
+  __syncthreads();
+  const int64_t r = i + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  if (r < n) a.U[IDX2(r, i, ld)] = (r == i) ? mkc(1.0, 0.0) : cmul(a.A[IDX2(r, i, a.lda)], hs.scal);
+}
+
+// 1c. part(c) = sum_{r in chunk, r >= i} conj(A(r, c)) u(r), c > i; warp per column
+__global__ void __launch_bounds__(BRB) bd_gemv_c(BdArgs a) {
+  __shared__ cplx us[BCH];
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
+  const int64_t r0 = i + (int64_t)blockIdx.y * BCH, r1 = min(r0 + BCH, n);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += BRB) us[r - r0] = a.U[IDX2(r, i, ld)];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = i + 1 + (int64_t)blockIdx.x * (BRB / 32) + warp;
+  if (c >= n) return;
+  cplx acc = mkc(0.0, 0.0);
+  const cplx* Ac = a.A + IDX2(0, c, a.lda);
+  for (int64_t r = r0 + lane; r < r1; r += 32) cfma_cj(acc, Ac[r], us[r - r0]);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) a.part[(c - i - 1) + blockIdx.y * ldp] = acc;
+}
+
+// generic small dot: out = sum_{r in [r0, n)} conj(col(r)) vec(r); one CTA per output
+__global__ void __launch_bounds__(BRB) bd_dots(BdArgs a, int64_t r0, int nA, const cplx* colA, int64_t offA,
+                                               int nB, const cplx* colB, int64_t offB, const cplx* vec, cplx* out) {
+  __shared__ double red[32];
+  BD_GUARD();
+  const int64_t n = a.n, ld = n;
+  const int which = blockIdx.x < nA ? 0 : 1;
+  const int q = which == 0 ? blockIdx.x : blockIdx.x - nA;
+  const cplx* col = which == 0 ? colA + (offA + q) * ld : colB + (offB + q) * ld;
+  cplx acc = mkc(0.0, 0.0);
+  for (int64_t r = r0 + threadIdx.x; r < n; r += BRB) cfma_cj(acc, col[r], vec[r]);
+  const double sx = bsum(acc.x, red);
+  const double sy = bsum(acc.y, red);
+  if (threadIdx.x == 0) out[which * NBB + q] = mkc(sx, sy);
+  (void)nB;
+}
+
+// 1d. y(c) = tauq (sum parts - Y s_U - V s_X), c > i -> Y(c, ii)
+__global__ void __launch_bounds__(BRB) bd_y_assemble(BdArgs a, int nch) {
+  __shared__ cplx su[NBB], sx[NBB];
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
+  const int ii = (int)(i - a.p);
+  if (threadIdx.x < ii) su[threadIdx.x] = a.s[threadIdx.x], sx[threadIdx.x] = a.s[NBB + threadIdx.x];
+  __syncthreads();
+  const int64_t c = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  if (c >= n) return;
+  cplx y = mkc(0.0, 0.0);
+  for (int k = 0; k < nch; ++k) y = cadd(y, a.part[(c - i - 1) + k * ldp]);
+  for (int q = 0; q < ii; ++q) {
+    y = csub(y, cmul(a.Y[IDX2(c, q, ld)], su[q]));
+    y = csub(y, cmul(a.Vr[IDX2(c, a.p + q, ld)], sx[q]));
+  }
+  a.Y[IDX2(c, ii, ld)] = cmul(a.tauq[i], y);
+}
+
+// 2a. row update (c > i), partial norms of c >= i+2
+__global__ void __launch_bounds__(BRB) bd_row_update(BdArgs a) {
+  __shared__ cplx ui[NBB], xi[NBB];
+  __shared__ double red[32];
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n;
+  const int ii = (int)(i - a.p);
+  if (threadIdx.x <= ii) ui[threadIdx.x] = a.U[IDX2(i, a.p + threadIdx.x, ld)];
+  if (threadIdx.x < ii) xi[threadIdx.x] = a.X[IDX2(i, threadIdx.x, ld)];
+  __syncthreads();
+  const int64_t c = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  double nrm = 0.0;
+  if (c < n) {
+    cplx r = a.A[IDX2(i, c, a.lda)];
+    for (int q = 0; q <= ii; ++q) r = csub(r, cmul(ui[q], cconj(a.Y[IDX2(c, q, ld)])));
+    for (int q = 0; q < ii; ++q) r = csub(r, cmul(xi[q], cconj(a.Vr[IDX2(c, a.p + q, ld)])));
+    a.A[IDX2(i, c, a.lda)] = r;
+    if (c >= i + 2) nrm = cabs2(r);
+  }
+  const double s = bsum(nrm, red);
+  if (threadIdx.x == 0) a.npart[blockIdx.x] = s;
+}
+
+// 2b. right reflector from x = conj(row), v into Vr(:, i) (rows >= i+1)
+__global__ void __launch_bounds__(BRB) bd_house_right(BdArgs a, int nparts) {
+  __shared__ BHouse hs;
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n;
+  if (threadIdx.x == 0) {
+    double x2 = 0.0;
+    for (int k = 0; k < nparts; ++k) x2 += a.npart[k];
+    hs = bmake_house(cconj(a.A[IDX2(i, i + 1, a.lda)]), x2);
+    if (blockIdx.x == 0) {
+      a.taup[i] = hs.tau;
+      a.e[i] = hs.beta;
+    }
+  }
+  __syncthreads();
+  const int64_t c = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  if (c < n) a.Vr[IDX2(c, i, ld)] = (c == i + 1) ? mkc(1.0, 0.0) : cmul(cconj(a.A[IDX2(i, c, a.lda)]), hs.scal);
+}
+
+// 2c. part(r) = sum_{c in chunk, c > i} A(r, c) v(c), r > i; thread per row
+__global__ void __launch_bounds__(BRB) bd_gemv_n(BdArgs a) {
+  __shared__ cplx vs[BCH];
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
+  const int64_t c0 = i + 1 + (int64_t)blockIdx.y * BCH, c1 = min(c0 + BCH, n);
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += BRB) vs[c - c0] = a.Vr[IDX2(c, i, ld)];
+  __syncthreads();
+  const int64_t r = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  if (r >= n) return;
+  cplx acc0 = mkc(0.0, 0.0), acc1 = mkc(0.0, 0.0);
+  const cplx* Ar = a.A + r;
+  int64_t c = c0;
+  for (; c + 1 < c1; c += 2) {
+    cfma(acc0, Ar[c * a.lda], vs[c - c0]);
+    cfma(acc1, Ar[(c + 1) * a.lda], vs[c + 1 - c0]);
+  }
+  if (c < c1) cfma(acc0, Ar[c * a.lda], vs[c - c0]);
+  a.part[(r - i - 1) + blockIdx.y * ldp] = cadd(acc0, acc1);
+}
+
+// 2d. x(r) = taup (sum parts - U s_Y - X s_V), r > i -> X(r, ii)
+__global__ void __launch_bounds__(BRB) bd_x_assemble(BdArgs a, int nch) {
+  __shared__ cplx sy[NBB], sv[NBB];
+  BD_GUARD();
+  const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
+  const int ii = (int)(i - a.p);
+  if (threadIdx.x <= ii) sy[threadIdx.x] = a.s[threadIdx.x];
+  if (threadIdx.x < ii) sv[threadIdx.x] = a.s[NBB + threadIdx.x];
+  __syncthreads();
+  const int64_t r = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
+  if (r >= n) return;
+  cplx x = mkc(0.0, 0.0);
+  for (int k = 0; k < nch; ++k) x = cadd(x, a.part[(r - i - 1) + k * ldp]);
+  for (int q = 0; q <= ii; ++q) x = csub(x, cmul(a.U[IDX2(r, a.p + q, ld)], sy[q]));
+  for (int q = 0; q < ii; ++q) x = csub(x, cmul(a.X[IDX2(r, q, ld)], sv[q]));
+  a.X[IDX2(r, ii, ld)] = cmul(a.taup[i], x);
+}
+
+#define BLAUNCH(kern, grid, ...)                 \
+  do {                                           \
+    kern<<<(grid), BRB, 0, s>>>(__VA_ARGS__);    \
+    bse_count_launch();                          \
+    BSE_LAUNCH_CHECK();                          \
+  } while (0)
+
+bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const GebrdWork& w,
+                       const int64_t* status) {
+  if (n <= 0) return BSE_OK;
+  const int64_t ld = n;
+  BSE_CUDA(cudaMemsetAsync(w.U, 0, sizeof(cplx) * n * n, s));
+  BSE_CUDA(cudaMemsetAsync(w.Vr, 0, sizeof(cplx) * n * n, s));
+  BdArgs a;
+  a.n = n, a.A = A, a.lda = lda, a.U = w.U, a.Vr = w.Vr, a.X = w.X, a.Y = w.Y;
+  a.tauq = w.tauq, a.taup = w.taup, a.d = w.d, a.e = w.e;
+  a.part = w.part;
+  a.npart = (double*)(w.part + bchunks(n) * (n + 1));
+  a.s = w.small;
+  a.status = status;
+  const cplx one = mkc(1.0, 0.0), mone = mkc(-1.0, 0.0);
+  for (int64_t p = 0; p < n; p += NBB) {
+    const int64_t bs = (n - p) < NBB ? (n - p) : NBB;
+    a.p = p;
+    for (int64_t i = p; i < p + bs; ++i) {
+      a.i = i;
+      const int ii = (int)(i - p);
+      const unsigned gr = ceil_div_u(n - i, BRB);
+      BLAUNCH(bd_col_update, gr, a);
+      BLAUNCH(bd_house_left, gr, a, (int)gr);
+      if (i == n - 1) break;
+      const int64_t m = n - i - 1;  // trailing columns / rows
+      // y = tauq (A^H u - Y (U^H u) - V (X^H u))
+      dim3 gc(ceil_div_u(m, BRB / 32), (unsigned)bchunks(n - i));
+      BLAUNCH(bd_gemv_c, gc, a);
+      if (ii > 0) BLAUNCH(bd_dots, 2 * ii, a, i, ii, w.U, p, ii, w.X, (int64_t)0, w.U + i * ld, w.small);
+      BLAUNCH(bd_y_assemble, ceil_div_u(m, BRB), a, (int)bchunks(n - i));
+      // row update and right reflector
+      const unsigned gm = ceil_div_u(m, BRB);
+      BLAUNCH(bd_row_update, gm, a);
+      BLAUNCH(bd_house_right, gm, a, (int)gm);
+      // x = taup (A v - U (Y^H v) - X (V^H v))
+      dim3 gn(ceil_div_u(m, BRB), (unsigned)bchunks(m));
+      BLAUNCH(bd_gemv_n, gn, a);
+      BLAUNCH(bd_dots, 2 * ii + 1, a, i + 1, ii + 1, w.Y, (int64_t)0, ii, w.Vr, p, w.Vr + i * ld, w.small);
+      BLAUNCH(bd_x_assemble, gm, a, (int)bchunks(m));
+    }
+    const int64_t t0 = p + bs, mt = n - t0;
+    if (mt > 0) {
+      cplx* A22 = A + IDX2(t0, t0, lda);
+      GemmParams<cplx> g1 = gemm_params<cplx>(mt, mt, bs, OPN, w.U + IDX2(t0, p, ld), ld, OPC,
+                                              w.Y + IDX2(t0, 0, ld), ld, mone, one, A22, lda);
+      g1.status = status;
+      bse_status r = gemm_z(s, g1);
+      if (r) return r;
+      GemmParams<cplx> g2 = gemm_params<cplx>(mt, mt, bs, OPN, w.X + IDX2(t0, 0, ld), ld, OPC,
+                                              w.Vr + IDX2(t0, p, ld), ld, mone, one, A22, lda);
+      g2.status = status;
+      if ((r = gemm_z(s, g2))) return r;
+    }
+  }
+  return BSE_OK;
+}
+
+bse_status gebrd_backtransform(cudaStream_t s, int side, int64_t n, int64_t k, const GebrdWork& w, cplx* Vout,
+                               int64_t ldv, cplx* tmp, const int64_t* status) {
+  const int64_t nref = side == 0 ? n : n - 1;  // number of reflectors
+  if (nref <= 0) return BSE_OK;
+  const int64_t npan = (nref + NBB - 1) / NBB;
+  for (int64_t b = npan - 1; b >= 0; --b) {
+    const int64_t p = b * NBB;
+    const int64_t bs = (nref - p) < NBB ? (nref - p) : NBB;
+    bse_status r = side == 0
+                       ? apply_block_reflector(s, n, k, w.U, n, p, bs, p, w.tauq, Vout, ldv, tmp, status)
+                       : apply_block_reflector(s, n, k, w.Vr, n, p, bs, p + 1, w.taup, Vout, ldv, tmp, status);
+    if (r) return r;
+  }
+  return BSE_OK;
+}

@@ -1,0 +1,384 @@
+// Householder reduction of the Hermitian M of Alg. 2 to a real symmetric
+// tridiagonal T = Q^H M Q (lower storage), and the back-transformation
+// V_M = Q Z of the eigenvectors Z of T.
+//
+// Blocked in panels of NBT columns.  Within a panel the matrix is kept as
+// panel-start A plus the correction -V W^H - W V^H (V: reflectors, W: their
+// images); column j of the panel
+//   1. receives the correction (tr_col_update) and the norm of its tail,
+//   2. gets the reflector H_j = I - tau v v^H with H_j^H x = beta e_1,
+//      beta real (tr_house), so T is real,
+//   3. w = tau (A22 v - V (W^H v) - W (V^H v)) with A22 v from the lower
+//      triangle in two coalesced passes (tr_hemv_lo, tr_hemv_up),
+//   4. w += -tau/2 (w^H v) v  -- so that H_j^H A H_j = A - v w^H - w v^H.
+// After the panel, the trailing lower triangle takes the rank-2*NBT update
+// through the GEMM engine.  On GB300 step 3 is bound by the FP64 pipe, not by
+// HBM (n'^2 complex MACs over n'^2 * 16 bytes needs 3.4 TFLOP/s to saturate
+// 6.8 TB/s; the part delivers 1.2), so the one-stage reduction does the same
+// FP64 work as a band reduction and saves its second back-transformation.
+#include "kernels.cuh"
+
+constexpr int NBT = 32;    // panel width
+constexpr int RB = 256;    // rows per CTA in column kernels
+constexpr int HCH = 512;   // column chunk of the Hermitian matvec
+
+int hetrd_panel() { return NBT; }
+static inline int64_t nchunks(int64_t m) { return (m + HCH - 1) / HCH; }
+size_t hetrd_part_elems(int64_t n) { return (size_t)(2 * nchunks(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64; }
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < (blockDim.x >> 5)) t = red[threadIdx.x];
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ cplx block_sum_c(cplx v, double* red) {
+  const double a = block_sum(v.x, red);
+  const double b = block_sum(v.y, red);
+  return mkc(a, b);
+}
+
+// 1. column update + norm partial sums of rows >= j+2
+__global__ void __launch_bounds__(RB) tr_col_update(int64_t n, int64_t p, int64_t j, cplx* __restrict__ A,
+                                                    int64_t lda, const cplx* __restrict__ V, int64_t ldv,
+                                                    const cplx* __restrict__ W, int64_t ldw, double* __restrict__ d,
+                                                    double* __restrict__ npart, const int64_t* status) {
+  __shared__ cplx vj[NBT], wj[NBT];
+  __shared__ double red[32];
+  if (*(volatile const int64_t*)status) return;
+  const int jj = (int)(j - p);
+  if (threadIdx.x < jj) {
+    vj[threadIdx.x] = V[IDX2(j, p + threadIdx.x, ldv)];
+    wj[threadIdx.x] = W[IDX2(j, threadIdx.x, ldw)];
+  }
+  __syncthreads();
+  const int64_t r = j + (int64_t)blockIdx.x * RB + threadIdx.x;
+  double nrm = 0.0;
+  if (r < n) {
+    cplx c = A[IDX2(r, j, lda)];
+    for (int q = 0; q < jj; ++q) {
+      // c -= V(r,q) conj(W(j,q)) + W(r,q) conj(V(j,q))
+      const cplx vr = V[IDX2(r, p + q, ldv)], wr = W[IDX2(r, q, ldw)];
+      const cplx a = cmul(vr, cconj(wj[q])), b = cmul(wr, cconj(vj[q]));
+      c = csub(c, cadd(a, b));
+    }
+    if (r == j) {
+      c.y = 0.0;
+      d[j] = c.x;
+    }
+    A[IDX2(r, j, lda)] = c;
+    if (r >= j + 2) nrm = cabs2(c);
+  }
+  const double s = block_sum(nrm, red);
+  if (threadIdx.x == 0) npart[blockIdx.x] = s;
+}
+
+// Reflector from alpha = x_0 and ||x_{1:}||^2: H^H x = beta e_1 with beta real,
+// H = I - tau v v^H, v_0 = 1, v_{1:} = x_{1:} / (alpha - beta).
+struct House {
+  cplx tau, scal;
+  double beta;
+};
+__device__ __forceinline__ House make_house(cplx alpha, double xnorm2) {
+  House h;
+  if (xnorm2 == 0.0 && alpha.y == 0.0) {
+    h.tau = mkc(0.0, 0.0);
+    h.beta = alpha.x;
+    h.scal = mkc(0.0, 0.0);
+  } else {
+    const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+    const double beta = (alpha.x >= 0.0) ? -nrm : nrm;
+    h.beta = beta;
+    h.tau = mkc((beta - alpha.x) / beta, -alpha.y / beta);
+    h.scal = cdiv(mkc(1.0, 0.0), mkc(alpha.x - beta, alpha.y));
+  }
+  return h;
+}
+
+// 2. reflector for column j, v written into V(:, j) (rows >= j+1)
+__global__ void __launch_bounds__(RB) tr_house(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
+                                               cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ tau,
+                                               double* __restrict__ e, const double* __restrict__ npart, int nparts,
+                                               const int64_t* status) {
+  __shared__ House hs;
+  if (*(volatile const int64_t*)status) return;
+  if (threadIdx.x == 0) {
+    double x2 = 0.0;
+    for (int i = 0; i < nparts; ++i) x2 += npart[i];
+    hs = make_house(A[IDX2(j + 1, j, lda)], x2);
+    if (blockIdx.x == 0) {
+      tau[j] = hs.tau;
+      e[j] = hs.beta;
+    }
+  }
+  __syncthreads();
+  const int64_t r = j + 1 + (int64_t)blockIdx.x * RB + threadIdx.x;
+  if (r < n) V[IDX2(r, j, ldv)] = (r == j + 1) ? mkc(1.0, 0.0) : cmul(A[IDX2(r, j, lda)], hs.scal);
+}
+
+// 3a. y1(r) = sum_{j+1 <= c <= r} A(r, c) v(c), partial over column chunks
+__global__ void __launch_bounds__(RB) tr_hemv_lo(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
+                                                 const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
+                                                 int64_t ldpart, const int64_t* status) {
+  __shared__ cplx vs[HCH];
+  if (*(volatile const int64_t*)status) return;
+  const int64_t base = j + 1;
+  const int64_t m = n - base;
+  const int64_t c0 = (int64_t)blockIdx.y * HCH;
+  const int64_t rb0 = (int64_t)blockIdx.x * RB;
+  const int64_t rmax = rb0 + RB - 1;
+  const int64_t r = rb0 + threadIdx.x;  // local row
+  if (c0 > rmax) {                      // chunk entirely above this row block
+    if (r < m) part[r + blockIdx.y * ldpart] = mkc(0.0, 0.0);
+    return;
+  }
+  const int64_t c1 = min(c0 + HCH, m);
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += RB) vs[c - c0] = V[IDX2(base + c, j, ldv)];
+  __syncthreads();
+  if (r >= m) return;
+  const int64_t cend = min(c1, r + 1);
+  cplx acc0 = mkc(0.0, 0.0), acc1 = mkc(0.0, 0.0);
+  const cplx* Ar = A + IDX2(base + r, base, lda);
+  int64_t c = c0;
+  for (; c + 1 < cend; c += 2) {
+    const cplx a0 = Ar[c * lda], a1 = Ar[(c + 1) * lda];
+    cfma(acc0, a0, vs[c - c0]);
+    cfma(acc1, a1, vs[c + 1 - c0]);
+  }
+  if (c < cend) cfma(acc0, Ar[c * lda], vs[c - c0]);
+  part[r + blockIdx.y * ldpart] = cadd(acc0, acc1);
+}
+
+// 3b. y2(c) = sum_{r > c} conj(A(r, c)) v(r), warp per column, partial over row chunks
+__global__ void __launch_bounds__(RB) tr_hemv_up(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
+                                                 const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
+                                                 int64_t ldpart, const int64_t* status) {
+  __shared__ cplx vs[HCH];
+  if (*(volatile const int64_t*)status) return;
+  const int64_t base = j + 1;
+  const int64_t m = n - base;
+  const int64_t r0 = (int64_t)blockIdx.y * HCH;
+  const int64_t r1 = min(r0 + HCH, m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * (RB / 32) + warp;  // local column
+  for (int64_t rr = r0 + threadIdx.x; rr < r1; rr += RB) vs[rr - r0] = V[IDX2(base + rr, j, ldv)];
+  __syncthreads();
+  if (c >= m) return;
+  cplx acc = mkc(0.0, 0.0);
+  const cplx* Ac = A + IDX2(base, base + c, lda);
+  for (int64_t rr = max(r0, c + 1) + lane; rr < r1; rr += 32) cfma_cj(acc, Ac[rr], vs[rr - r0]);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) part[c + blockIdx.y * ldpart] = acc;
+}
+
+// 3c. s1 = W^H v, s2 = V_panel^H v over rows >= j+1 (one CTA per output)
+__global__ void __launch_bounds__(RB) tr_panel_dots(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
+                                                    int64_t ldv, const cplx* __restrict__ W, int64_t ldw,
+                                                    cplx* __restrict__ s12, const int64_t* status) {
+  __shared__ double red[32];
+  if (*(volatile const int64_t*)status) return;
+  const int jj = (int)(j - p);
+  const int q = blockIdx.x % jj, which = blockIdx.x / jj;  // which 0: W, 1: V
+  const cplx* col = which == 0 ? W + IDX2(0, q, ldw) : V + IDX2(0, p + q, ldv);
+  cplx acc = mkc(0.0, 0.0);
+  for (int64_t r = j + 1 + threadIdx.x; r < n; r += RB) cfma_cj(acc, col[r], V[IDX2(r, j, ldv)]);
+  const cplx s = block_sum_c(acc, red);
+  if (threadIdx.x == 0) s12[which * NBT + q] = s;
+}
+
+// 3d. w = tau (y1 + y2 - V s1 - W s2), stored in W(:, jj); partial sums of w^H v
+__global__ void __launch_bounds__(RB) tr_w_assemble(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
+                                                    int64_t ldv, cplx* __restrict__ W, int64_t ldw,
+                                                    const cplx* __restrict__ part, int64_t ldpart, int nch,
+                                                    const cplx* __restrict__ s12, const cplx* __restrict__ tau,
+                                                    double* __restrict__ dpart, const int64_t* status) {
+  __shared__ cplx s1[NBT], s2[NBT];
+  __shared__ double red[32];
+  if (*(volatile const int64_t*)status) return;
+  const int jj = (int)(j - p);
+  if (threadIdx.x < jj) {
+    s1[threadIdx.x] = s12[threadIdx.x];
+    s2[threadIdx.x] = s12[NBT + threadIdx.x];
+  }
+  __syncthreads();
+  const int64_t base = j + 1, m = n - base;
+  const int64_t r = (int64_t)blockIdx.x * RB + threadIdx.x;
+  cplx dot = mkc(0.0, 0.0);
+  if (r < m) {
+    cplx y = mkc(0.0, 0.0);
+    for (int c = 0; c < nch; ++c) {
+      y = cadd(y, part[r + c * ldpart]);
+      y = cadd(y, part[r + (nch + c) * ldpart]);
+    }
+    const int64_t gr = base + r;
+    for (int q = 0; q < jj; ++q) {
+      y = csub(y, cmul(V[IDX2(gr, p + q, ldv)], s1[q]));
+      y = csub(y, cmul(W[IDX2(gr, q, ldw)], s2[q]));
+    }
+    y = cmul(tau[j], y);
+    W[IDX2(gr, jj, ldw)] = y;
+    dot = cmul(cconj(y), V[IDX2(gr, j, ldv)]);
+  }
+  const cplx s = block_sum_c(dot, red);
+  if (threadIdx.x == 0) {
+    dpart[2 * blockIdx.x] = s.x;
+    dpart[2 * blockIdx.x + 1] = s.y;
+  }
+}
+
+// 4. w += -tau/2 (w^H v) v
+__global__ void __launch_bounds__(RB) tr_w_finish(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
+                                                  int64_t ldv, cplx* __restrict__ W, int64_t ldw,
+                                                  const cplx* __restrict__ tau, const double* __restrict__ dpart,
+                                                  int nparts, const int64_t* status) {
+  __shared__ cplx alpha;
+  if (*(volatile const int64_t*)status) return;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nparts; ++i) a += dpart[2 * i], b += dpart[2 * i + 1];
+    alpha = cscale(cmul(tau[j], mkc(a, b)), -0.5);
+  }
+  __syncthreads();
+  const int jj = (int)(j - p);
+  const int64_t r = j + 1 + (int64_t)blockIdx.x * RB + threadIdx.x;
+  if (r < n) W[IDX2(r, jj, ldw)] = cadd(W[IDX2(r, jj, ldw)], cmul(alpha, V[IDX2(r, j, ldv)]));
+}
+
+__global__ void tr_last_diag(int64_t n, const cplx* A, int64_t lda, double* d, const int64_t* status) {
+  if (*(volatile const int64_t*)status) return;
+  d[n - 1] = A[IDX2(n - 1, n - 1, lda)].x;
+}
+
+#define LAUNCH(kern, grid, blk, ...)                 \
+  do {                                               \
+    kern<<<(grid), (blk), 0, s>>>(__VA_ARGS__);      \
+    bse_count_launch();                              \
+    BSE_LAUNCH_CHECK();                              \
+  } while (0)
+
+bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const HetrdWork& w,
+                       const int64_t* status) {
+  if (n <= 0) return BSE_OK;
+  const int64_t ldv = n, ldw = n;
+  BSE_CUDA(cudaMemsetAsync(w.V, 0, sizeof(cplx) * n * n, s));
+  const int64_t ldpart = n + 1;
+  cplx* part = w.part;                                     // 2 * nchunks columns of length ldpart
+  double* npart = (double*)(w.part + 2 * nchunks(n) * ldpart);
+  double* dpart = npart + (n / RB + 2);
+  cplx* s12 = w.small;
+  const cplx one = mkc(1.0, 0.0), mone = mkc(-1.0, 0.0);
+  for (int64_t p = 0; p < n - 1; p += NBT) {
+    const int64_t bs = (n - 1 - p) < NBT ? (n - 1 - p) : NBT;
+    for (int64_t j = p; j < p + bs; ++j) {
+      const int64_t m = n - j - 1;  // length of the reflector
+      const unsigned g1 = ceil_div_u(n - j, RB);
+      LAUNCH(tr_col_update, g1, RB, n, p, j, A, lda, w.V, ldv, w.W, ldw, w.d, npart, status);
+      const unsigned g2 = ceil_div_u(m, RB);
+      LAUNCH(tr_house, g2, RB, n, j, A, lda, w.V, ldv, w.tau, w.e, npart, (int)g1, status);
+      const int64_t nch = nchunks(m);
+      dim3 glo(ceil_div_u(m, RB), (unsigned)nch);
+      LAUNCH(tr_hemv_lo, glo, RB, n, j, A, lda, w.V, ldv, part, ldpart, status);
+      dim3 gup(ceil_div_u(m, RB / 32), (unsigned)nch);
+      LAUNCH(tr_hemv_up, gup, RB, n, j, A, lda, w.V, ldv, part + nch * ldpart, ldpart, status);
+      const int jj = (int)(j - p);
+      if (jj > 0) LAUNCH(tr_panel_dots, 2 * jj, RB, n, p, j, w.V, ldv, w.W, ldw, s12, status);
+      LAUNCH(tr_w_assemble, g2, RB, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, s12, w.tau, dpart,
+             status);
+      LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)g2, status);
+    }
+    const int64_t t0 = p + bs, mt = n - t0;
+    if (mt > 0) {
+      // A22 -= V W^H + W V^H  (lower triangle of rows/cols >= t0)
+      cplx* A22 = A + IDX2(t0, t0, lda);
+      GemmParams<cplx> g1 = gemm_params<cplx>(mt, mt, bs, OPN, w.V + IDX2(t0, p, ldv), ldv, OPC,
+                                              w.W + IDX2(t0, 0, ldw), ldw, mone, one, A22, lda);
+      g1.lowerC = 1;
+      g1.status = status;
+      bse_status r = gemm_z(s, g1);
+      if (r) return r;
+      GemmParams<cplx> g2p = gemm_params<cplx>(mt, mt, bs, OPN, w.W + IDX2(t0, 0, ldw), ldw, OPC,
+                                               w.V + IDX2(t0, p, ldv), ldv, mone, one, A22, lda);
+      g2p.lowerC = 1;
+      g2p.status = status;
+      r = gemm_z(s, g2p);
+      if (r) return r;
+    }
+  }
+  LAUNCH(tr_last_diag, 1, 1, n, A, lda, w.d, status);
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Block reflector application (columnwise, forward order):
+//   H_c0 ... H_{c0+bs-1} = I - Vp T Vp^H,  T upper triangular with
+//   T(i,i) = tau_i,  T(0:i, i) = -tau_i T(0:i, 0:i) (Vp(:, 0:i)^H v_i).
+__global__ void larft_kernel(int bs, const cplx* __restrict__ G, int ldg, const cplx* __restrict__ tau,
+                             cplx* __restrict__ T, int ldt, const int64_t* status) {
+  if (*(volatile const int64_t*)status) return;
+  const int r = threadIdx.x;
+  for (int e = r; e < bs * bs; e += blockDim.x) T[(e % bs) + (e / bs) * ldt] = mkc(0.0, 0.0);
+  __syncthreads();
+  for (int i = 0; i < bs; ++i) {
+    if (r < i) {
+      cplx acc = mkc(0.0, 0.0);
+      for (int q = r; q < i; ++q) cfma(acc, T[r + q * ldt], G[q + i * ldg]);
+      T[r + i * ldt] = cmul(cscale(tau[i], -1.0), acc);
+    } else if (r == i) {
+      T[i + i * ldt] = tau[i];
+    }
+    __syncthreads();
+  }
+}
+
+bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cplx* Vbuf, int64_t ldvb, int64_t c0,
+                                 int64_t bs, int64_t r0, const cplx* tau, cplx* Vout, int64_t ldv, cplx* tmp,
+                                 const int64_t* status) {
+  if (bs <= 0 || k <= 0 || r0 >= n) return BSE_OK;
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), mone = mkc(-1.0, 0.0);
+  const int64_t m = n - r0;
+  const cplx* Vp = Vbuf + IDX2(r0, c0, ldvb);
+  cplx* G = tmp;                 // bs x bs
+  cplx* T = G + bs * bs;         // bs x bs
+  cplx* W1 = T + bs * bs;        // bs x k
+  cplx* W2 = W1 + bs * k;        // bs x k
+  GemmParams<cplx> pg = gemm_params<cplx>(bs, bs, m, OPC, Vp, ldvb, OPN, Vp, ldvb, one, zero, G, bs);
+  pg.status = status;
+  bse_status r = gemm_z(s, pg);
+  if (r) return r;
+  larft_kernel<<<1, 64, 0, s>>>((int)bs, G, (int)bs, tau + c0, T, (int)bs, status);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  GemmParams<cplx> p1 = gemm_params<cplx>(bs, k, m, OPC, Vp, ldvb, OPN, Vout + r0, ldv, one, zero, W1, bs);
+  p1.status = status;
+  if ((r = gemm_z(s, p1))) return r;
+  GemmParams<cplx> p2 = gemm_params<cplx>(bs, k, bs, OPN, T, bs, OPN, W1, bs, one, zero, W2, bs);
+  p2.triA = TRI_UP;
+  p2.status = status;
+  if ((r = gemm_z(s, p2))) return r;
+  GemmParams<cplx> p3 = gemm_params<cplx>(m, k, bs, OPN, Vp, ldvb, OPN, W2, bs, mone, one, Vout + r0, ldv);
+  p3.status = status;
+  return gemm_z(s, p3);
+}
+
+bse_status hetrd_backtransform(cudaStream_t s, int64_t n, int64_t k, const HetrdWork& w, cplx* Vout, int64_t ldv,
+                               cplx* tmp, const int64_t* status) {
+  if (n <= 1) return BSE_OK;
+  const int64_t npan = (n - 1 + NBT - 1) / NBT;
+  for (int64_t b = npan - 1; b >= 0; --b) {
+    const int64_t p = b * NBT;
+    const int64_t bs = (n - 1 - p) < NBT ? (n - 1 - p) : NBT;
+    bse_status r = apply_block_reflector(s, n, k, w.V, n, p, bs, p + 1, w.tau, Vout, ldv, tmp, status);
+    if (r) return r;
+  }
+  return BSE_OK;
+}

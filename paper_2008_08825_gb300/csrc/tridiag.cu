@@ -1,0 +1,255 @@
+// Eigenpairs of a real symmetric tridiagonal matrix T (diagonal a, off-
+// diagonal off), the "D" and "V_M" of Alg. 2 after the Householder
+// reduction, and -- in Golub-Kahan form (zero diagonal, off = d1, e1, d2, e2,
+// ..., size 2n) -- the singular triplets of the bidiagonal of Alg. 3.
+//
+//  * splitting: off(k) with |off(k)| <= eps * ||T|| is set to 0 and T is
+//    treated block by block (Golub-Kahan form: only at the e positions, so
+//    every block keeps even size and its +-sigma pairing);
+//  * eigenvalues: Sturm-count bisection, one thread per eigenvalue, to
+//    relative width 2 eps (for the Golub-Kahan form this is bisection on the
+//    singular values, which keeps their high relative accuracy);
+//  * eigenvectors: one thread per eigenvalue solves with the twisted
+//    factorisation T - lambda I = N_r D_r N_r^T (top-down and bottom-up
+//    pivots, twist index r = argmin |gamma_r|): z_r = 1 and the two
+//    recurrences outward -- one step of inverse iteration from the best unit
+//    vector;
+//  * orthogonalisation: one Newton-Schulz step Z <- Z (3I - Z^T Z)/2 (two
+//    FP64 GEMMs) brings the O(eps ||T|| / gap) loss of orthogonality of close
+//    eigenvalues down to O(eps) without changing the residuals beyond O(eps ||T||).
+#include <float.h>
+
+#include "kernels.cuh"
+
+// prm: 0 pivmin, 1 tnorm, 2 twist guard, 3 lower bound, 4 upper bound
+// iprm: 0 number of blocks
+__global__ void tri_prep_kernel(int64_t N, const double* __restrict__ a_in, const double* __restrict__ off_in, int mode,
+                                double* __restrict__ a, double* __restrict__ off, double* __restrict__ e2,
+                                int* __restrict__ bstart, double* __restrict__ prm, int* __restrict__ iprm) {
+  __shared__ double red_t[32], red_e[32], red_lo[32], red_hi[32];
+  __shared__ double tnorm_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double tn = 0.0, em = 0.0, lo = 1e308, hi = -1e308;
+  for (int64_t k = tid; k < N; k += nt) {
+    const double ak = a_in ? a_in[k] : 0.0;
+    const double ol = (k > 0) ? fabs(off_in[k - 1]) : 0.0;
+    const double orr = (k < N - 1) ? fabs(off_in[k]) : 0.0;
+    tn = fmax(tn, fabs(ak) + ol + orr);
+    lo = fmin(lo, ak - ol - orr);
+    hi = fmax(hi, ak + ol + orr);
+    if (k < N - 1) em = fmax(em, off_in[k] * off_in[k]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((tid & 31) == 0) red_t[tid >> 5] = tn, red_e[tid >> 5] = em, red_lo[tid >> 5] = lo, red_hi[tid >> 5] = hi;
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < nt / 32; ++w)
+      tn = fmax(tn, red_t[w]), em = fmax(em, red_e[w]), lo = fmin(lo, red_lo[w]), hi = fmax(hi, red_hi[w]);
+    const double pivmin = DBL_MIN * fmax(1.0, em);
+    prm[0] = pivmin;
+    prm[1] = tn;
+    prm[2] = DBL_EPSILON * fmax(tn, DBL_MIN);
+    const double pad = 2.0 * DBL_EPSILON * tn + 4.0 * pivmin;
+    prm[3] = lo - pad;
+    prm[4] = hi + pad;
+    tnorm_s = tn;
+  }
+  __syncthreads();
+  const double tol = DBL_EPSILON * tnorm_s;
+  for (int64_t k = tid; k < N; k += nt) {
+    a[k] = a_in ? a_in[k] : 0.0;
+    if (k < N - 1) {
+      double o = off_in[k];
+      const bool may_split = (mode == 0) || (k & 1);
+      if (may_split && fabs(o) <= tol) o = 0.0;
+      off[k] = o;
+      e2[k] = o * o;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nb = 0;
+    bstart[0] = 0;
+    for (int64_t k = 0; k < N - 1; ++k)
+      if (off[k] == 0.0) bstart[++nb] = (int)(k + 1);
+    bstart[++nb] = (int)N;
+    iprm[0] = nb;
+  }
+}
+
+__device__ __forceinline__ int sturm_count(const double* __restrict__ a, const double* __restrict__ e2, int b0, int b1,
+                                           double x, double pivmin) {
+  double q = a[b0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = q < 0.0;
+  for (int k = b0 + 1; k < b1; ++k) {
+    q = (a[k] - x) - e2[k - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+// slot s -> (block, local target index): mode 0 slots follow bstart,
+// mode 1 slots follow bstart / 2 and take the upper half of each block.
+__device__ __forceinline__ int find_block(const int* bstart, int nb, int64_t s, int mode) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int64_t st = mode == 0 ? bstart[mid] : bstart[mid] / 2;
+    if (st <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void tri_bisect_kernel(int64_t total, const double* __restrict__ a, const double* __restrict__ e2,
+                                  const int* __restrict__ bstart, const int* __restrict__ iprm,
+                                  const double* __restrict__ prm, int mode, double* __restrict__ lam,
+                                  int* __restrict__ blk, const int64_t* status) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= total) return;
+  if (*(volatile const int64_t*)status) return;
+  const int nb = iprm[0];
+  const int b = find_block(bstart, nb, s, mode);
+  const int b0 = bstart[b], b1 = bstart[b + 1];
+  const int m = b1 - b0;
+  const int t = mode == 0 ? (int)(s - b0) : m / 2 + (int)(s - b0 / 2);
+  const double pivmin = prm[0];
+  double lo = prm[3], hi = prm[4];
+  for (int it = 0; it < 256; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double w = hi - lo;
+    if (w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || w <= 4.0 * pivmin || mid == lo || mid == hi) break;
+    if (sturm_count(a, e2, b0, b1, mid, pivmin) > t) hi = mid; else lo = mid;
+  }
+  lam[s] = 0.5 * (lo + hi);
+  blk[s] = b;
+}
+
+__global__ void tri_rank_kernel(int64_t total, const double* __restrict__ lam, const int* __restrict__ iprm,
+                                int* __restrict__ rank) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= total) return;
+  if (iprm[0] == 1) {
+    rank[s] = (int)s;
+    return;
+  }
+  const double v = lam[s];
+  int r = 0;
+  for (int64_t t = 0; t < total; ++t) {
+    const double u = lam[t];
+    r += (u < v) || (u == v && t < s);
+  }
+  rank[s] = r;
+}
+
+// eigenvalues in ascending order for the selected range, and the vectors
+__global__ void tri_vec_kernel(int64_t total, int64_t il, int64_t iu, const double* __restrict__ a,
+                               const double* __restrict__ off, const double* __restrict__ e2,
+                               const int* __restrict__ bstart, const double* __restrict__ prm,
+                               const double* __restrict__ lam, const int* __restrict__ blk,
+                               const int* __restrict__ rank, double* __restrict__ lam_out, double* __restrict__ Z,
+                               int64_t ldz, double* __restrict__ scratch, int64_t ldsc, const int64_t* status) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= total) return;
+  if (*(volatile const int64_t*)status) return;
+  const int64_t rk = rank[s];
+  if (rk < il || rk > iu) return;
+  const int64_t col = rk - il;
+  const double l = lam[s];
+  lam_out[col] = l;
+  if (!Z) return;
+  const int b = blk[s];
+  const int b0 = bstart[b], b1 = bstart[b + 1];
+  const int m = b1 - b0;
+  const double g = prm[2];
+  double* zc = Z + col * ldz + b0;
+  double* sc = scratch + col * ldsc + b0;
+  // pass 1: top-down pivots dp(k) (stored in zc)
+  double x = a[b0] - l;
+  if (fabs(x) < g) x = (x < 0.0) ? -g : g;
+  zc[0] = x;
+  for (int k = 1; k < m; ++k) {
+    x = (a[b0 + k] - l) - e2[b0 + k - 1] / x;
+    if (fabs(x) < g) x = (x < 0.0) ? -g : g;
+    zc[k] = x;
+  }
+  // pass 2: bottom-up pivots dm(k) (stored in sc) and the twist index
+  double y = a[b1 - 1] - l;
+  if (fabs(y) < g) y = (y < 0.0) ? -g : g;
+  sc[m - 1] = y;
+  double best = fabs(zc[m - 1]);
+  int r = m - 1;
+  for (int k = m - 2; k >= 0; --k) {
+    const double ak = a[b0 + k] - l;
+    y = ak - e2[b0 + k] / y;
+    if (fabs(y) < g) y = (y < 0.0) ? -g : g;
+    sc[k] = y;
+    const double gam = zc[k] + y - ak;
+    if (fabs(gam) < best) best = fabs(gam), r = k;
+  }
+  // pass 3: the vector
+  double nrm2 = 1.0;
+  double z = 1.0;
+  for (int k = r - 1; k >= 0; --k) {
+    z = -(off[b0 + k] / zc[k]) * z;
+    zc[k] = z;
+    nrm2 += z * z;
+  }
+  zc[r] = 1.0;
+  z = 1.0;
+  for (int k = r; k < m - 1; ++k) {
+    z = -(off[b0 + k] / sc[k + 1]) * z;
+    zc[k + 1] = z;
+    nrm2 += z * z;
+  }
+  const double inv = 1.0 / sqrt(nrm2);
+  for (int k = 0; k < m; ++k) zc[k] *= inv;
+}
+
+bse_status orthonormalize_columns(cudaStream_t s, int64_t N, int64_t k, double* Z, int64_t ldz, const TriWork& w,
+                                  const int64_t* status) {
+  if (k <= 0 || N <= 0) return BSE_OK;
+  // E = Z^T Z - I;  Z <- Z - 0.5 Z E
+  GemmParams<double> pe = gemm_params<double>(k, k, N, OPT, Z, ldz, OPN, Z, ldz, 1.0, 0.0, w.E, k);
+  pe.status = status;
+  bse_status r = gemm_d(s, pe);
+  if (r) return r;
+  if ((r = sub_identity(s, k, w.E, k))) return r;
+  BSE_CUDA(cudaMemcpy2DAsync(w.Z2, sizeof(double) * N, Z, sizeof(double) * ldz, sizeof(double) * N, k,
+                             cudaMemcpyDeviceToDevice, s));
+  GemmParams<double> pz = gemm_params<double>(N, k, k, OPN, Z, ldz, OPN, w.E, k, -0.5, 1.0, w.Z2, N);
+  pz.status = status;
+  if ((r = gemm_d(s, pz))) return r;
+  BSE_CUDA(cudaMemcpy2DAsync(Z, sizeof(double) * ldz, w.Z2, sizeof(double) * N, sizeof(double) * N, k,
+                             cudaMemcpyDeviceToDevice, s));
+  return BSE_OK;
+}
+
+bse_status tridiag_eig(cudaStream_t s, int64_t N, const double* a, const double* off, int mode, int64_t il,
+                       int64_t iu, double* lam_out, double* Z, int64_t ldz, const TriWork& w, int64_t* status) {
+  if (N <= 0) return BSE_OK;
+  const int64_t total = mode == 0 ? N : N / 2;
+  const int64_t k = iu - il + 1;
+  tri_prep_kernel<<<1, 1024, 0, s>>>(N, a, off, mode, w.a, w.off, w.e2, w.bstart, w.prm, w.iprm);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  tri_bisect_kernel<<<ceil_div_u(total, 64), 64, 0, s>>>(total, w.a, w.e2, w.bstart, w.iprm, w.prm, mode, w.lam,
+                                                         w.blk, status);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  tri_rank_kernel<<<ceil_div_u(total, 256), 256, 0, s>>>(total, w.lam, w.iprm, w.rank);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  if (Z) BSE_CUDA(cudaMemset2DAsync(Z, sizeof(double) * ldz, 0, sizeof(double) * N, k, s));
+  tri_vec_kernel<<<ceil_div_u(total, 64), 64, 0, s>>>(total, il, iu, w.a, w.off, w.e2, w.bstart, w.prm, w.lam,
+                                                      w.blk, w.rank, lam_out, Z, ldz, w.scratch, N, status);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
