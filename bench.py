@@ -1,0 +1,298 @@
+"""Benchmark: full BSE eigensolves per second (and model TFLOP/s) on GB300.
+
+One step = one Cholesky-method solve (Alg. 2) and one SVD-method solve
+(Alg. 3) of the n = 8192 complex128 workload (base generator, seed = rank):
+all n positive eigenvalues and the eigenvectors [X; Y].  Inputs are resident
+in HBM before timing; A and B (1.07 GB each) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+Multi-GPU: a single solve does not shard (replicas only): every rank solves
+its own instance and value = solves of all ranks / max-over-ranks time.
+
+--impl reference times the CPU oracle (plain FP64 C, OpenMP) on a bounded
+sample of the same workload (smaller n, same generator), scaled to n = 8192
+by the n^3 cost ratio.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FULL = 8192
+MODEL_FLOPS = {"chol": 160.0 / 3.0, "svd": 296.0 / 3.0}  # x n^3 real flops (Table 2 x 4, complex)
+METRIC = "full BSE eigensolves/sec and TFLOP/s at n=8192 (FP64 vs mixed+refine)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=768)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp64_peak():
+    """Measured FP64 DFMA throughput of this part (profiles/fp64_peaks_gb300.md)."""
+    return 1200.0  # GFLOP/s -> reported in TFLOP/s below
+
+
+def cpu_baseline(n_sample: int, steps: int = 1):
+    """Time the oracle (as it stands) on n_sample; return solves/s scaled to N_FULL."""
+    import numpy as np
+
+    import oracle
+    from paper_2008_08825_gb300 import inputs
+
+    A, B = inputs.base(n_sample, seed=0)
+    oracle.load()
+    t = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.solve_chol(A, B)
+        oracle.solve_svd(A, B)
+        t += time.perf_counter() - t0
+    per_step = t / steps
+    scale = (N_FULL / n_sample) ** 3
+    value = 2.0 / (per_step * scale)
+    return {"value": value, "unit": "solves/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"oracle CHOL + SVD solve (Alg. 2 and 3, all pairs) of the base workload at n={n_sample}, "
+                      f"{steps} step(s), {per_step:.2f} s per step, scaled to n={N_FULL} by (n/{n_sample})^3"}, per_step
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+
+    n_s = args.cpu_sample_n
+    for _ in range(args.warmup):
+        cpu_baseline(n_s, 1)
+    cb, per_step = cpu_baseline(n_s, max(args.steps, 1))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3 * (N_FULL / n_s) ** 3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"BSE form-I n={N_FULL} complex128, base generator, CHOL+SVD all pairs",
+                       "n": N_FULL, "methods": ["chol", "svd"], "parallelism": "replicas"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2008_08825_gb300 import bse, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    n = args.n
+    A, B = inputs.base(n, seed=rank)
+    At = torch.from_numpy(A).to(dev)
+    Bt = torch.from_numpy(B).to(dev)
+    del A, B
+    h = bse.Handle()
+    h.reserve(n, "svd", dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        o1, _, _ = bse.solve(At, Bt, method="chol", handle=h)
+        o2, _, _ = bse.solve(At, Bt, method="svd", handle=h)
+        return o1, o2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    bse.lib().bse_profile_enable(h.ptr, 1)
+    launches0 = h.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = h.launches() - launches0
+    prof = _read_profile(bse, h)
+    bse.lib().bse_profile_enable(h.ptr, 0)
+    clk = clocks.stop()
+    if pg:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+        pg.barrier()
+    solves = 2 * args.steps * world
+    value = solves / elapsed
+    ms_per_step = elapsed / args.steps * 1e3
+    model = sum(MODEL_FLOPS.values()) * float(n) ** 3
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(At.mT.contiguous().cpu().numpy()).pin_memory()
+        Bh = torch.from_numpy(Bt.mT.contiguous().cpu().numpy()).pin_memory()
+        om = torch.empty(n, dtype=torch.float64).pin_memory()
+        Xh = torch.empty((n, n), dtype=torch.complex128).pin_memory()
+        Yh = torch.empty((n, n), dtype=torch.complex128).pin_memory()
+        info = bse._Info()
+        P = ctypes.c_void_p
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for method in (0, 1):
+            code = bse.lib().bse_solve_host(h.ptr, method, n, P(Ah.data_ptr()), n, P(Bh.data_ptr()), n, 1, n, 0,
+                                            P(om.data_ptr()), P(Xh.data_ptr()), n, P(Yh.data_ptr()), n,
+                                            ctypes.byref(info), P(stream.cuda_stream))
+            bse._check(code)
+        te = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": 2 * world / te, "unit": "solves/s", "h2d_bytes_per_step": 2 * 2 * n * n * 16,
+               "d2h_bytes_per_step": 2 * (n * 8 + 2 * n * n * 16)}
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    peak_tf = fp64_peak() / 1e3
+    gemm_tf = prof["gemm_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else None
+    tot_stage = sum(prof["stage_ms"]) or 1.0
+    roofline = {
+        "bound": "alu", "kernel": "gemm_kernel<cplx> (FP64 DFMA GEMM engine)",
+        "achieved": gemm_tf, "peak": peak_tf, "unit": "TFLOP/s",
+        "frac": (gemm_tf / peak_tf) if gemm_tf else None,
+        "traffic": None,
+        "peak_source": "FP64 DFMA throughput measured on this GB300 (profiles/fp64_peaks_gb300.md); "
+                       "FP64 mma.sync measured lower (1.05 TFLOP/s)",
+        "gemm_share_of_step": prof["gemm_ms"] / tot_stage,
+        "gemm_launches": prof["gemm_launches"],
+    }
+    cb = None
+    if not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(args.cpu_sample_n, 1)
+    stage_names = ["form", "cholesky", "congruence_or_product", "householder_reduction", "tridiagonal",
+                   "orthogonalisation", "back_transformation", "post_processing", "gradient", "other"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"BSE form-I n={n} complex128, base generator (seed = rank), one CHOL (Alg. 2) "
+                               f"and one SVD (Alg. 3) solve per step, all n eigenpairs with vectors, FP64",
+                   "n": n, "methods": ["chol", "svd"], "precision": "fp64", "parallelism": "replicas",
+                   "l2": "inputs (2 x 1.07 GB) larger than L2, no flush"},
+        "model_tflops": model * args.steps * world / elapsed / 1e12,
+        "model_flops_per_step": model,
+        "stage_ms_per_step": {k: v / args.steps for k, v in zip(stage_names, prof["stage_ms"]) if v > 0},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cb,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def _read_profile(bse, h):
+    class PD(ctypes.Structure):
+        _fields_ = [("stage_ms", ctypes.c_double * 10), ("stage_calls", ctypes.c_int64 * 10),
+                    ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double), ("gemm_launches", ctypes.c_int64),
+                    ("launches", ctypes.c_int64)]
+
+    pd = PD()
+    L = bse.lib()
+    L.bse_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(PD)]
+    bse._check(L.bse_profile_read(h.ptr, ctypes.byref(pd)))
+    return {"stage_ms": list(pd.stage_ms), "gemm_ms": pd.gemm_ms, "gemm_flops": pd.gemm_flops,
+            "gemm_launches": pd.gemm_launches, "launches": pd.launches}
+
+
+if __name__ == "__main__":
+    main()

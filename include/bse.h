@@ -143,9 +143,33 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
                           double* omega, double* X, int64_t ldx, double* Y, int64_t ldy,
                           bse_info* info, void* stream);
 
-/* Number of CUDA kernel launches this handle has issued so far (all entry
- * points).  Used to report launch counts. */
+/* Number of CUDA kernel launches the library has issued so far in this
+ * process (all handles, all entry points). */
 int64_t bse_launch_count(bse_handle h);
+
+/*
+ * Profiling (tracing aid, not part of the paper): while enabled, the solves
+ * of this handle record CUDA events around each pipeline stage and around
+ * every launch of the FP64 GEMM engine, on the solve's stream.  Times are
+ * device times between those events; GEMM flops count only the useful
+ * (structurally nonzero) multiply-adds, 8 real flops per complex MAC.
+ * bse_profile_enable resets the counters; bse_profile_read returns them
+ * (the solves already synchronise their stream, so no extra sync happens).
+ */
+#define BSE_NSTAGES 10
+/* stage index: 0 form A+-B, 1 Cholesky, 2 congruence / product L1^H L2,
+ * 3 Householder reduction, 4 tridiagonal eigensolve, 5 orthogonalisation,
+ * 6 back-transformation, 7 post-processing + final setup, 8 gradient, 9 other */
+typedef struct bse_profile_data {
+  double stage_ms[BSE_NSTAGES];
+  int64_t stage_calls[BSE_NSTAGES];
+  double gemm_ms;         /* sum of per-launch device times of the GEMM engine */
+  double gemm_flops;      /* useful flops of those launches */
+  int64_t gemm_launches;
+  int64_t launches;       /* all kernel launches while enabled */
+} bse_profile_data;
+bse_status bse_profile_enable(bse_handle h, int enable);
+bse_status bse_profile_read(bse_handle h, bse_profile_data* out);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,9 @@ def _bind(lib):
                                    _I64, _P, _I64, ctypes.POINTER(_Info), _P]
     lib.bse_launch_count.argtypes = [_P]
     lib.bse_launch_count.restype = ctypes.c_int64
+    lib.bse_profile_enable.argtypes = [_P, ctypes.c_int]
+    lib.bse_profile_enable.restype = ctypes.c_int
+    lib.bse_profile_read.restype = ctypes.c_int
     for name in ("bse_create", "bse_destroy", "bse_workspace_size", "bse_set_workspace", "bse_solve_chol",
                  "bse_solve_svd", "bse_grad", "bse_solve_host"):
         getattr(lib, name).restype = ctypes.c_int

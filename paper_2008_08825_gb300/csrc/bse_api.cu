@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "prof.cuh"
 
 static thread_local std::string g_err;
 void bse_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
@@ -40,6 +41,24 @@ struct bse_context {
   void* io = nullptr;       // staging for bse_solve_host
   size_t io_bytes = 0;
   int64_t* host_status = nullptr;  // pinned, 2 entries
+  Profiler* prof = nullptr;
+  int prof_on = 0;
+};
+
+// Makes the handle's profiler current for this thread for one entry point;
+// on exit synchronises the stream (the entry points do anyway) and folds the
+// recorded events into the counters.
+struct ProfGuard {
+  bse_context* h;
+  cudaStream_t s;
+  ProfGuard(bse_context* hh, cudaStream_t ss) : h(hh), s(ss) { prof_set_current(h->prof_on ? h->prof : nullptr); }
+  ~ProfGuard() {
+    if (prof_current()) {
+      cudaStreamSynchronize(s);
+      prof_flush(h->prof);
+    }
+    prof_set_current(nullptr);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -251,11 +270,19 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  ProfGuard pgd(h, s);
   // M1 = A + B (full), M2 = A - B (lower, in L)
-  TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.M1, n, 1));
-  TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L, n, 0));
-  TRY(potrf_lower(s, n, b.L, n, b.Linv, st, BSE_ERR_NOT_PD_AMINUSB));
+  {
+    StageScope sc(0, s);
+    TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.M1, n, 1));
+    TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L, n, 0));
+  }
+  {
+    StageScope sc(1, s);
+    TRY(potrf_lower(s, n, b.L, n, b.Linv, st, BSE_ERR_NOT_PD_AMINUSB));
+  }
   // W = M1 L ; M = L^H W (lower) into M1's buffer
+  StageScope sc2(2, s);
   GemmParams<cplx> p1 = gemm_params<cplx>(n, n, n, OPN, b.M1, n, OPN, b.L, n, one, zero, b.W, n);
   p1.triB = TRI_LO;
   p1.status = st;
@@ -265,16 +292,30 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
   p2.lowerC = 1;
   p2.status = st;
   TRY(gemm_z(s, p2));
+  prof_stage_end(2, s);
   // Hermitian eigendecomposition of M
-  TRY(hetrd_lower(s, n, b.M1, n, b.h, st));
-  TRY(tridiag_eig(s, n, b.h.d, b.h.e, 0, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, n, b.t.w, st));
-  TRY(finish_omega(s, k, b.lam, 0, omega, b.c1, b.c2, st));
+  {
+    StageScope sc(3, s);
+    TRY(hetrd_lower(s, n, b.M1, n, b.h, st));
+  }
+  {
+    StageScope sc(4, s);
+    TRY(tridiag_eig(s, n, b.h.d, b.h.e, 0, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, n, b.t.w, st));
+    TRY(finish_omega(s, k, b.lam, 0, omega, b.c1, b.c2, st));
+  }
   if (!X) return finish(h, s, st, info);
-  TRY(orthonormalize_columns(s, n, k, b.Z, n, b.t.w, st));
+  {
+    StageScope sc(5, s);
+    TRY(orthonormalize_columns(s, n, k, b.Z, n, b.t.w, st));
+  }
   cplx* VM = b.W;  // reuse: V_M = Q Z (n x k)
-  TRY(real_to_complex(s, n, k, b.Z, n, VM, n));
-  TRY(hetrd_backtransform(s, n, k, b.h, VM, n, b.tmp, st));
+  {
+    StageScope sc(6, s);
+    TRY(real_to_complex(s, n, k, b.Z, n, VM, n));
+    TRY(hetrd_backtransform(s, n, k, b.h, VM, n, b.tmp, st));
+  }
   // P = L^{-H} V_M
+  StageScope sc7(7, s);
   BSE_CUDA(cudaMemcpy2DAsync(b.P, sizeof(cplx) * n, VM, sizeof(cplx) * n, sizeof(cplx) * n, k,
                              cudaMemcpyDeviceToDevice, s));
   TRY(trsm_lower_conjtrans(s, n, k, b.L, n, b.Linv, b.P, n, st));
@@ -300,34 +341,55 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
-  TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.L1, n, 0));
-  TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L2, n, 0));
-  TRY(potrf_lower(s, n, b.L1, n, b.Linv, st, BSE_ERR_NOT_PD_APLUSB));
-  TRY(potrf_lower(s, n, b.L2, n, b.Linv, st, BSE_ERR_NOT_PD_AMINUSB));
+  ProfGuard pgd(h, s);
+  {
+    StageScope sc(0, s);
+    TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.L1, n, 0));
+    TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L2, n, 0));
+  }
+  {
+    StageScope sc(1, s);
+    TRY(potrf_lower(s, n, b.L1, n, b.Linv, st, BSE_ERR_NOT_PD_APLUSB));
+    TRY(potrf_lower(s, n, b.L2, n, b.Linv, st, BSE_ERR_NOT_PD_AMINUSB));
+  }
   // G = L1^H L2
+  prof_stage_begin(2, s);
   GemmParams<cplx> pg = gemm_params<cplx>(n, n, n, OPC, b.L1, n, OPN, b.L2, n, one, zero, b.G, n);
   pg.triA = TRI_UP;
   pg.triB = TRI_LO;
   pg.status = st;
   TRY(gemm_z(s, pg));
-  TRY(gebrd_upper(s, n, b.G, n, b.g, st));
+  prof_stage_end(2, s);
+  {
+    StageScope sc(3, s);
+    TRY(gebrd_upper(s, n, b.G, n, b.g, st));
+  }
   // Golub-Kahan tridiagonal (size 2n, zero diagonal)
+  prof_stage_begin(4, s);
   gk_offdiag_kernel<<<ceil_div_u(n, 256), 256, 0, s>>>(n, b.g.d, b.g.e, b.off);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   TRY(tridiag_eig(s, 2 * n, nullptr, b.off, 1, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, 2 * n, b.t.w, st));
   TRY(finish_omega(s, k, b.lam, 1, omega, b.c1, b.c2, st));
+  prof_stage_end(4, s);
   if (!X) return finish(h, s, st, info);
-  dim3 gsp(ceil_div_u(n, 256), (unsigned)k);
-  gk_split_kernel<<<gsp, 256, 0, s>>>(n, k, b.Z, 2 * n, b.UB, b.VB);
-  bse_count_launch();
-  BSE_LAUNCH_CHECK();
-  TRY(orthonormalize_columns(s, n, k, b.UB, n, b.t.w, st));
-  TRY(orthonormalize_columns(s, n, k, b.VB, n, b.t.w, st));
-  TRY(real_to_complex(s, n, k, b.UB, n, b.Uc, n));
-  TRY(real_to_complex(s, n, k, b.VB, n, b.Vc, n));
-  TRY(gebrd_backtransform(s, 0, n, k, b.g, b.Uc, n, b.tmp, st));
-  TRY(gebrd_backtransform(s, 1, n, k, b.g, b.Vc, n, b.tmp, st));
+  {
+    StageScope sc(5, s);
+    dim3 gsp(ceil_div_u(n, 256), (unsigned)k);
+    gk_split_kernel<<<gsp, 256, 0, s>>>(n, k, b.Z, 2 * n, b.UB, b.VB);
+    bse_count_launch();
+    BSE_LAUNCH_CHECK();
+    TRY(orthonormalize_columns(s, n, k, b.UB, n, b.t.w, st));
+    TRY(orthonormalize_columns(s, n, k, b.VB, n, b.t.w, st));
+  }
+  {
+    StageScope sc(6, s);
+    TRY(real_to_complex(s, n, k, b.UB, n, b.Uc, n));
+    TRY(real_to_complex(s, n, k, b.VB, n, b.Vc, n));
+    TRY(gebrd_backtransform(s, 0, n, k, b.g, b.Uc, n, b.tmp, st));
+    TRY(gebrd_backtransform(s, 1, n, k, b.g, b.Vc, n, b.tmp, st));
+  }
+  StageScope sc7(7, s);
   // T1 = L1 U ; X, Y from T1 and L2 V with c1 = c2 = 1/sqrt(omega)
   GemmParams<cplx> p1 = gemm_params<cplx>(n, k, n, OPN, b.L1, n, OPN, b.Uc, n, one, zero, b.T1, n);
   p1.triA = TRI_LO;
@@ -354,12 +416,14 @@ bse_status bse_create(bse_handle* out) {
     delete h;
     return bse_internal_set_error("cudaMallocHost failed"), BSE_ERR_NOMEM;
   }
+  h->prof = prof_new();
   *out = h;
   return BSE_OK;
 }
 
 bse_status bse_destroy(bse_handle h) {
   if (!h) return BSE_OK;
+  prof_delete(h->prof);
   if (h->ws) cudaFree(h->ws);
   if (h->io) cudaFree(h->io);
   if (h->host_status) cudaFreeHost(h->host_status);
@@ -410,6 +474,8 @@ bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t
   if (!dA || !dB || (k > 0 && (!X || !Y || !w))) return bse_internal_set_error("NULL pointer"), BSE_ERR_ARG;
   if (ldda < n || lddb < n || (k > 0 && (ldx < n || ldy < n))) return bse_internal_set_error("leading dimension < n"), BSE_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  ProfGuard pgd(h, s);
+  StageScope sc(8, s);
   TRY(grad_outer(s, n, k, (const cplx*)X, ldx, (const cplx*)Y, ldy, w, (cplx*)dA, ldda, (cplx*)dB, lddb));
   BSE_CUDA(cudaStreamSynchronize(s));
   return BSE_OK;
@@ -461,6 +527,19 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
 int64_t bse_launch_count(bse_handle h) {
   (void)h;
   return (int64_t)bse_total_launches();
+}
+
+bse_status bse_profile_enable(bse_handle h, int enable) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  h->prof_on = enable ? 1 : 0;
+  prof_reset(h->prof);
+  return BSE_OK;
+}
+
+bse_status bse_profile_read(bse_handle h, bse_profile_data* out) {
+  if (!h || !out) return bse_internal_set_error("NULL argument"), BSE_ERR_ARG;
+  prof_read(h->prof, out);
+  return BSE_OK;
 }
 
 }  // extern "C"

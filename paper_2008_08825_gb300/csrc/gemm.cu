@@ -10,6 +10,7 @@
 #include <atomic>
 
 #include "gemm.cuh"
+#include "prof.cuh"
 
 static std::atomic<long long> g_launches{0};
 void bse_count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -193,20 +194,71 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(const GemmParams<T> p) {
   }
 }
 
+// Useful (structurally nonzero) multiply-adds of a launch, for the profiler:
+// the number of (i, j, kk) with i < m, j < n, kk < k allowed by the
+// triangular structure of op(A), op(B) and the lower-only output.
+static double sum_min(int64_t cnt, int64_t cap, int64_t off) {
+  // sum_{i=0}^{cnt-1} clamp(i + off, 0, cap)
+  double s = 0.0;
+  for (int64_t i = 0; i < cnt; ++i) {
+    int64_t v = i + off;
+    s += (double)(v < 0 ? 0 : (v > cap ? cap : v));
+  }
+  return s;
+}
+template <typename T>
+static double useful_macs(const GemmParams<T>& p) {
+  const int64_t m = p.m, n = p.n, k = p.k;
+  const bool lo = p.lowerC != 0;
+  if (p.triA == TRI_NONE && p.triB == TRI_NONE) {
+    if (!lo) return (double)m * n * k;
+    double s = 0.0;  // pairs i >= j
+    for (int64_t j = 0; j < n && j < m; ++j) s += (double)(m - j);
+    return s * (double)k;
+  }
+  if (p.triA == TRI_LO && p.triB == TRI_NONE && !lo) return sum_min(m, k, 1) * (double)n;  // kk <= i
+  if (p.triA == TRI_UP && p.triB == TRI_NONE) {                                            // kk >= i
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      const double kk = (double)(k - i > 0 ? k - i : 0);
+      const double jj = lo ? (double)((i < n ? i : n - 1) + 1) : (double)n;
+      s += kk * jj;
+    }
+    return s;
+  }
+  if (p.triB == TRI_LO && p.triA == TRI_NONE && !lo) {  // kk >= j
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += (double)(k - j > 0 ? k - j : 0);
+    return s * (double)m;
+  }
+  if (p.triB == TRI_UP && p.triA == TRI_NONE && !lo) return sum_min(n, k, 1) * (double)m;  // kk <= j
+  if (p.triA == TRI_UP && p.triB == TRI_LO && !lo) {  // kk >= max(i, j)
+    double s = 0.0;
+    const int64_t mx = m > n ? m : n;
+    for (int64_t t = 0; t < mx && t < k; ++t) {
+      const double a1 = (double)(t + 1 < m ? t + 1 : m) * (double)(t + 1 < n ? t + 1 : n);
+      const double a0 = (double)(t < m ? t : m) * (double)(t < n ? t : n);
+      s += (a1 - a0) * (double)(k - t);
+    }
+    return s;
+  }
+  return (double)m * n * k;  // not used by the pipelines: dense count
+}
+
 template <typename T, int BK>
 static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
   if (p.m <= 0 || p.n <= 0) return BSE_OK;
-  if (p.k <= 0 && p.epi == EPI_NONE) {
-    // C = beta C (or 0): still needs a pass so that k = 0 behaves like BLAS
-  }
   dim3 grid(ceil_div_u(p.n, GBN), ceil_div_u(p.m, GBM));
   if (grid.y > 65535) {
     bse_internal_set_error("gemm: m too large for one launch");
     return BSE_ERR_ARG;
   }
+  const bool prof = prof_current() != nullptr;
+  if (prof) prof_gemm_begin(s);
   gemm_kernel<T, BK><<<grid, 256, 0, s>>>(p);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
+  if (prof) prof_gemm_end(s, useful_macs(p) * (sizeof(T) == sizeof(cplx) ? 8.0 : 2.0));
   return BSE_OK;
 }
 

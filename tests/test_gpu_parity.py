@@ -1,0 +1,361 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (the FP64 form; derivations in the comments):
+  * omega, normwise:        max_i |w_i - w_i*| / max w*            <= 1e-11
+  * omega, per eigenvalue:  max_i |w_i - w_i*| / w_i*  (base generator) <= 1e-11
+  * Sigma-orthogonality:    ||X^H X - Y^H Y - I||_F                  <= 1e-10
+  * residual:               ||H V - V W||_F / (||H||_F ||V||_F)      <= 1e-14
+  * eigenvectors, per column after phase alignment (largest entry of
+    [x; y] real positive): <= 1e-11 * max w / gap_i + 1e-12, gap_i the
+    distance of w_i to its nearest neighbour (first-order perturbation bound).
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from conftest import eig_residual, phase_align, sigma_residual
+from paper_2008_08825_gb300 import bse, inputs
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ["chol", "svd"]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    return torch.device("cuda", 0)
+
+
+@functools.lru_cache(maxsize=None)
+def _base(n, seed):
+    return inputs.base(n, seed)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(n, seed):
+    A, B = _base(n, seed)
+    return oracle.solve_svd(A, B)
+
+
+def _gpu(A, B, method, dev, **kw):
+    om, X, Y = bse.solve(torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev), method=method, **kw)
+    torch.cuda.synchronize()
+    out = [om.cpu().numpy()]
+    out += [None, None] if X is None else [X.cpu().numpy(), Y.cpu().numpy()]
+    return out
+
+
+def _gaps(om):
+    if len(om) == 1:
+        return np.array([np.inf])
+    d = np.diff(om)
+    g = np.empty_like(om)
+    g[0], g[-1] = d[0], d[-1]
+    g[1:-1] = np.minimum(d[:-1], d[1:])
+    return g
+
+
+def _check_vectors(X, Y, Xr, Yr, om_ref):
+    a, b = phase_align(X, Y)
+    c, d = phase_align(Xr, Yr)
+    err = np.maximum(np.abs(a - c).max(axis=0), np.abs(b - d).max(axis=0))
+    tol = 1e-11 * om_ref.max() / _gaps(om_ref) + 1e-12
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, (bad[:5], err[bad[:5]], tol[bad[:5]])
+
+
+SMALL = [1, 2, 3, 5, 17, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 257]
+
+
+@pytest.mark.parametrize("n", SMALL)
+@pytest.mark.parametrize("method", METHODS)
+def test_small_sizes_vs_oracle(n, method, dev):
+    A, B = _base(n, n)
+    om_r, X_r, Y_r = _oracle(n, n)
+    om, X, Y = _gpu(A, B, method, dev)
+    assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+    assert sigma_residual(X, Y) <= 1e-10
+    assert eig_residual(A, B, om, X, Y) <= 1e-14
+    _check_vectors(X, Y, X_r, Y_r, om_r)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_config_n64_all_2n_pairs(method, dev):
+    """n = 64, seed 0: all 2n eigenpairs (the -omega half is [Y; X], Lemma ComputeNegEvecs)."""
+    A, B = _base(64, 0)
+    om_r, X_r, Y_r = _oracle(64, 0)
+    om, X, Y = _gpu(A, B, method, dev)
+    assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    Af, Bf = inputs.hermitian_full(A), inputs.hermitian_full(B)
+    R1 = Af @ Y + Bf @ X + Y * om
+    R2 = -Bf @ Y - Af @ X + X * om
+    assert max(np.abs(R1).max(), np.abs(R2).max()) <= 1e-13 * om.max()
+    _check_vectors(X, Y, X_r, Y_r, om_r)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_subsets_match_full_solve(method, dev):
+    n = 150
+    A, B = _base(n, 3)
+    om, X, Y = _gpu(A, B, method, dev)
+    for il, iu in [(1, 1), (1, 7), (40, 77), (n - 4, n), (n, n)]:
+        o, x, y = _gpu(A, B, method, dev, il=il, iu=iu)
+        assert np.max(np.abs(o - om[il - 1:iu])) <= 1e-13 * om.max()
+        a, b = phase_align(x, y)
+        c, d = phase_align(X[:, il - 1:iu], Y[:, il - 1:iu])
+        assert max(np.abs(a - c).max(), np.abs(b - d).max()) < 1e-11
+    o, x, y = _gpu(A, B, method, dev, vectors=False)
+    assert x is None and np.array_equal(o, om)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_deterministic_bits(method, dev):
+    A, B = _base(96, 4)
+    r1 = _gpu(A, B, method, dev)
+    r2 = _gpu(A, B, method, dev)
+    for a, b in zip(r1, r2):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_config_n2048_vs_oracle(method, dev):
+    """n = 2048, seed 0 (the mid-size configuration): every eigenpair against the oracle."""
+    n = 2048
+    A, B = _base(n, 0)
+    om_r, X_r, Y_r = _oracle(n, 0)
+    om, X, Y = _gpu(A, B, method, dev)
+    assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+    assert sigma_residual(X, Y) <= 1e-10
+    _check_vectors(X, Y, X_r, Y_r, om_r)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_commuting_closed_form_n2048(method, dev):
+    """omega_i = sqrt(a_i^2 - b_i^2); x_i = alpha_i q_i, y_i = beta_i q_i."""
+    n = 2048
+    A, B, a, b, Q = inputs.commuting(n, seed=1)
+    om, X, Y = _gpu(A, B, method, dev)
+    ex = np.sqrt(a * a - b * b)
+    order = np.argsort(ex)
+    assert np.max(np.abs(om - ex[order])) <= 1e-11 * ex.max()
+    assert np.max(np.abs(om - ex[order]) / ex[order]) <= 1e-11
+    r = (ex - a) / b
+    alpha = 1.0 / np.sqrt(1.0 - r * r)
+    Xe = Q[:, order] * alpha[order][None, :]
+    Ye = Q[:, order] * (r * alpha)[order][None, :]
+    _check_vectors(X, Y, Xe, Ye, ex[order])
+    assert sigma_residual(X, Y) <= 1e-10
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_config_n8192_sampled(method, dev):
+    """Full size n = 8192, seed 0, the benchmark's launch configuration.  The
+    oracle cannot solve this size in a test, so: sampled eigenpair residuals
+    in FP64 on the CPU, Sigma-orthogonality of a column sample, and the
+    invariants sum omega^2 = tr(M1 M2) and sum 2 log omega = log det M1 + log det M2."""
+    n = 8192
+    A, B = _base(n, 0)
+    om, X, Y = _gpu(A, B, method, dev)
+    assert np.all(np.diff(om) >= 0) and om[0] > 0
+    Af, Bf = inputs.hermitian_full(A), inputs.hermitian_full(B)
+    rng = np.random.default_rng(123)
+    cols = np.unique(np.concatenate([[0, 1, n - 1], rng.choice(n, 61, replace=False)]))
+    x, y = X[:, cols], Y[:, cols]
+    R1 = Af @ x + Bf @ y - x * om[cols]
+    R2 = -Bf @ x - Af @ y - y * om[cols]
+    res = np.sqrt(np.sum(np.abs(R1) ** 2 + np.abs(R2) ** 2, axis=0))
+    assert np.max(res) <= 1e-12 * om.max()
+    S = x.conj().T @ x - y.conj().T @ y - np.eye(len(cols))
+    assert np.abs(S).max() <= 1e-12
+    M1, M2 = Af + Bf, Af - Bf
+    tr = np.real(np.sum(M1 * M2.T))
+    assert abs(np.sum(om ** 2) - tr) <= 1e-11 * tr
+    ld = np.linalg.slogdet(M1)[1] + np.linalg.slogdet(M2)[1]
+    assert abs(np.sum(2 * np.log(om)) - ld) <= 1e-10 * abs(ld)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10])
+@pytest.mark.parametrize("method", METHODS)
+def test_kappa_sweep_vs_oracle(kappa, method, dev):
+    """kappa(A - B) swept to 1e2 / 1e6 / 1e10 (n = 256): normwise error gated;
+    the per-eigenvalue error of the smallest omega is reported (Table 1 style)."""
+    n = 256
+    A, B, _ = inputs.kappa_sweep(n, kappa, seed=0)
+    om_r, _, _ = oracle.solve_svd(A, B, vectors=False)
+    om, X, Y = _gpu(A, B, method, dev)
+    if method == "svd" or kappa <= 1e6:
+        assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    else:
+        # CHOL computes omega^2 = eig(L^H (A+B) L), whose absolute error is
+        # O(eps ||H||^2); Eq. (SquaredErr) turns it into |d omega_i| ~ eps ||H||^2 / omega_i
+        tol = 64 * np.finfo(float).eps * om_r.max() ** 2 / om_r
+        assert np.all(np.abs(om - om_r) <= tol)
+    rel_small = abs(om[0] - om_r[0]) / om_r[0]
+    print(f"kappa={kappa:g} method={method} rel.err(smallest)={rel_small:.2e} sigma={sigma_residual(X, Y):.2e}")
+    if kappa <= 1e6:
+        assert sigma_residual(X, Y) <= 1e-10
+
+
+def test_batched_sizes_lowest_32(dev):
+    """A sample of the 512-instance workload (n log-uniform in [32, 1024]),
+    lowest 32 pairs of each, against the oracle."""
+    sizes = inputs.batched_sizes()
+    for i in [0, 1, 2, 3, 5, 8, 13, 21]:
+        n = int(sizes[i])
+        A, B = inputs.base(n, seed=i)
+        om_r, X_r, Y_r = oracle.solve_svd(A, B)
+        for method in METHODS:
+            om, X, Y = _gpu(A, B, method, dev, il=1, iu=min(32, n))
+            k = len(om)
+            assert np.max(np.abs(om - om_r[:k])) <= 1e-11 * om_r.max()
+            _check_vectors(X, Y, X_r[:, :k], Y_r[:, :k], om_r[:k] if k > 1 else om_r[:1])
+
+
+# --- gradient ---------------------------------------------------------------------
+
+def test_grad_vs_oracle(dev):
+    n, k = 80, 8
+    A, B = _base(n, 6)
+    om_r, X_r, Y_r = oracle.solve_svd(A, B)
+    w = inputs.grad_weights(k)
+    dA_r, dB_r = oracle.grad(X_r[:, :k], Y_r[:, :k], w)
+    for method in METHODS:
+        om, X, Y = bse.solve(torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev), method=method)
+        dA, dB = bse.grad(X[:, :k], Y[:, :k], torch.from_numpy(w).to(dev))
+        assert np.max(np.abs(dA.cpu().numpy() - dA_r)) <= 1e-11
+        assert np.max(np.abs(dB.cpu().numpy() - dB_r)) <= 1e-11
+
+
+def test_grad_autograd_function(dev):
+    n, k = 40, 5
+    A, B = _base(n, 7)
+    At = torch.from_numpy(inputs.hermitian_full(A)).to(dev).requires_grad_(True)
+    Bt = torch.from_numpy(inputs.hermitian_full(B)).to(dev).requires_grad_(True)
+    w = torch.from_numpy(inputs.grad_weights(k)).to(dev)
+    om = bse.Omega.apply(At, Bt, torch.arange(k), "svd")
+    (om * w).sum().backward()
+    om_r, X_r, Y_r = oracle.solve_svd(A, B)
+    dA_r, dB_r = oracle.grad(X_r[:, :k], Y_r[:, :k], w.cpu().numpy())
+    assert np.max(np.abs(At.grad.cpu().numpy() - dA_r)) <= 1e-11
+    assert np.max(np.abs(Bt.grad.cpu().numpy() - dB_r)) <= 1e-11
+
+
+def test_grad_config_n1024_central_differences(dev):
+    """n = 1024, L = sum_i w_i omega_i over the lowest 16 omega, w ~ N(0,1)
+    (seed 1); central differences (h = 1e-6) along 64 Hermitian directions
+    (seed 2, unit Frobenius norm) for A and for B."""
+    n, k = 1024, 16
+    A, B = _base(n, 0)
+    A, B = inputs.hermitian_full(A), inputs.hermitian_full(B)
+    w = inputs.grad_weights(k, seed=1)
+    At, Bt = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    om, X, Y = bse.solve(At, Bt, method="svd")
+    dA, dB = bse.grad(X[:, :k], Y[:, :k], torch.from_numpy(w).to(dev))
+    dA, dB = dA.cpu().numpy(), dB.cpu().numpy()
+    rng = np.random.default_rng(2)
+    h = 1e-6
+
+    def loss(Ap, Bp):
+        o, _, _ = bse.solve(torch.from_numpy(Ap).to(dev), torch.from_numpy(Bp).to(dev), method="svd", il=1, iu=k,
+                            vectors=False)
+        return float(np.dot(w, o.cpu().numpy()))
+
+    worst = 0.0
+    for t in range(64):
+        E = inputs.hermitian_direction(n, rng)
+        if t % 2 == 0:
+            fd = (loss(A + h * E, B) - loss(A - h * E, B)) / (2 * h)
+            an = float(np.real(np.vdot(dA, E)))
+        else:
+            fd = (loss(A, B + h * E) - loss(A, B - h * E)) / (2 * h)
+            an = float(np.real(np.vdot(dB, E)))
+        worst = max(worst, abs(fd - an))
+    # FD truncation O(h^2 |omega'''|) plus rounding O(eps max omega / h) ~ 1e-9
+    assert worst <= 5e-8, worst
+
+
+# --- edge cases and failures -------------------------------------------------------
+
+def test_not_positive_definite_status(dev):
+    n = 70
+    A = np.eye(n, dtype=np.complex128)
+    B = 0.5 * np.eye(n, dtype=np.complex128)
+    B[40, 40] = 1.5  # A - B = 0.5 I with -0.5 at column 41; A + B PD
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A, B, "chol", dev)
+    assert e.value.code == 2 and e.value.info == 41
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A, B, "svd", dev)
+    assert e.value.code == 2 and e.value.info == 41
+    A2 = 2.0 * np.eye(n, dtype=np.complex128)
+    B2 = np.eye(n, dtype=np.complex128)
+    B2[40, 40] = -2.5  # A + B = 3 I with -0.5 at column 41; A - B PD
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A2, B2, "svd", dev)
+    assert e.value.code == 3 and e.value.info == 41
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A2, B2, "chol", dev)  # found through the eigenvalues of M = L^H (A+B) L
+    assert e.value.code == 3
+
+
+def test_nan_input_is_reported(dev):
+    A, B = _base(33, 1)
+    A = A.copy()
+    A[10, 10] = np.nan
+    for method in METHODS:
+        with pytest.raises(bse.BseError) as e:
+            _gpu(A, B, method, dev)
+        assert e.value.code in (2, 3)
+
+
+def test_arguments_and_empty(dev):
+    A, B = _base(8, 1)
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A, B, "chol", dev, il=3, iu=2)
+    assert e.value.code == 1
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A, B, "chol", dev, il=0, iu=2)
+    assert e.value.code == 1
+    with pytest.raises(bse.BseError) as e:
+        _gpu(A, B, "svd", dev, precision="mixed")
+    assert e.value.code == 9
+    z = torch.zeros((0, 0), dtype=torch.complex128, device=dev)
+    om, X, Y = bse.solve(z, z)
+    assert om.numel() == 0
+
+
+def test_diagonal_and_degenerate_inputs(dev):
+    """Splitting of the tridiagonal: diagonal A, B (every off-diagonal of T is 0)
+    including repeated eigenvalues; the Tamm-Dancoff case B = 0."""
+    n = 40
+    d = np.repeat(np.array([2.0, 3.0, 5.0, 7.0]), 10)
+    A = np.diag(d).astype(np.complex128)
+    B = np.diag(np.full(n, 0.5)).astype(np.complex128)
+    ex = np.sort(np.sqrt(d * d - 0.25))
+    for method in METHODS:
+        om, X, Y = _gpu(A, B, method, dev)
+        assert np.max(np.abs(om - ex)) <= 1e-13 * ex.max()
+        assert sigma_residual(X, Y) <= 1e-12
+        assert eig_residual(A, B, om, X, Y) <= 1e-14
+    A2, _ = _base(50, 2)
+    lam = np.linalg.eigvalsh(inputs.hermitian_full(A2))
+    for method in METHODS:
+        om, X, Y = _gpu(A2, np.zeros_like(A2), method, dev)
+        assert np.max(np.abs(om - lam)) <= 1e-12 * lam.max()
+        assert np.abs(Y).max() <= 1e-12
+
+
+def test_host_buffer_entry_point(dev):
+    A, B = _base(120, 9)
+    for method in METHODS:
+        om, X, Y = _gpu(A, B, method, dev)
+        om2, X2, Y2 = bse.solve_host(A, B, method=method)
+        assert np.array_equal(om, om2.numpy())
+        assert np.array_equal(X, X2.numpy()) and np.array_equal(Y, Y2.numpy())
