@@ -90,6 +90,7 @@ struct TriPlan {
     w.iprm = pl.take<int>(8);
     w.scratch = pl.take<double>((size_t)N * k);
     w.E = pl.take<double>((size_t)k * k);
+    w.Ef = pl.take<float>((size_t)k * k);
     w.Z2 = pl.take<double>((size_t)N * k);
   }
 };
@@ -123,7 +124,7 @@ static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k) {
   b.lam = pl.take<double>(k);
   b.c1 = pl.take<double>(k);
   b.c2 = pl.take<double>(k);
-  b.tmp = pl.take<cplx>(2 * 64 * 64 + 2 * 64 * (size_t)k);
+  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
 }
 
 struct SvdBuffers {
@@ -163,7 +164,7 @@ static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k) {
   b.lam = pl.take<double>(k);
   b.c1 = pl.take<double>(k);
   b.c2 = pl.take<double>(k);
-  b.tmp = pl.take<cplx>(2 * 64 * 64 + 2 * 64 * (size_t)k);
+  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
 }
 
 static size_t plan_bytes(int64_t n, int64_t k, int method) {

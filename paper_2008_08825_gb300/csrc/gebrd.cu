@@ -135,9 +135,18 @@ __global__ void __launch_bounds__(BRB) bd_gemv_c(BdArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = i + 1 + (int64_t)blockIdx.x * (BRB / 32) + warp;
   if (c >= n) return;
-  cplx acc = mkc(0.0, 0.0);
+  cplx accs[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
   const cplx* Ac = a.A + IDX2(0, c, a.lda);
-  for (int64_t r = r0 + lane; r < r1; r += 32) cfma_cj(acc, Ac[r], us[r - r0]);
+  int64_t r = r0 + lane;
+  for (; r + 96 < r1; r += 128) {
+    cplx av[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ac + r + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma_cj(accs[u], av[u], us[r + 32 * u - r0]);
+  }
+  for (; r < r1; r += 32) cfma_cj(accs[0], Ac[r], us[r - r0]);
+  cplx acc = cadd(cadd(accs[0], accs[1]), cadd(accs[2], accs[3]));
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -233,15 +242,18 @@ __global__ void __launch_bounds__(BRB) bd_gemv_n(BdArgs a) {
   __syncthreads();
   const int64_t r = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
   if (r >= n) return;
-  cplx acc0 = mkc(0.0, 0.0), acc1 = mkc(0.0, 0.0);
+  cplx acc[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
   const cplx* Ar = a.A + r;
   int64_t c = c0;
-  for (; c + 1 < c1; c += 2) {
-    cfma(acc0, Ar[c * a.lda], vs[c - c0]);
-    cfma(acc1, Ar[(c + 1) * a.lda], vs[c + 1 - c0]);
+  for (; c + 3 < c1; c += 4) {
+    cplx av[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ar + (c + u) * a.lda);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma(acc[u], av[u], vs[c + u - c0]);
   }
-  if (c < c1) cfma(acc0, Ar[c * a.lda], vs[c - c0]);
-  a.part[(r - i - 1) + blockIdx.y * ldp] = cadd(acc0, acc1);
+  for (; c < c1; ++c) cfma(acc[0], Ar[c * a.lda], vs[c - c0]);
+  a.part[(r - i - 1) + blockIdx.y * ldp] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
 // 2d. x(r) = taup (sum parts - U s_Y - X s_V), r > i -> X(r, ii)
@@ -330,10 +342,11 @@ bse_status gebrd_backtransform(cudaStream_t s, int side, int64_t n, int64_t k, c
                                int64_t ldv, cplx* tmp, const int64_t* status) {
   const int64_t nref = side == 0 ? n : n - 1;  // number of reflectors
   if (nref <= 0) return BSE_OK;
-  const int64_t npan = (nref + NBB - 1) / NBB;
+  const int64_t bt = backtransform_block();
+  const int64_t npan = (nref + bt - 1) / bt;
   for (int64_t b = npan - 1; b >= 0; --b) {
-    const int64_t p = b * NBB;
-    const int64_t bs = (nref - p) < NBB ? (nref - p) : NBB;
+    const int64_t p = b * bt;
+    const int64_t bs = (nref - p) < bt ? (nref - p) : bt;
     bse_status r = side == 0
                        ? apply_block_reflector(s, n, k, w.U, n, p, bs, p, w.tauq, Vout, ldv, tmp, status)
                        : apply_block_reflector(s, n, k, w.Vr, n, p, bs, p + 1, w.taup, Vout, ldv, tmp, status);

@@ -29,6 +29,16 @@ struct Num<double> {
   __device__ __forceinline__ static double rs(double a, double s) { return a * s; }
 };
 template <>
+struct Num<float> {
+  __device__ __forceinline__ static float zero() { return 0.0f; }
+  __device__ __forceinline__ static float cj(float a) { return a; }
+  __device__ __forceinline__ static void fma_(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+  __device__ __forceinline__ static float mul(float a, float b) { return a * b; }
+  __device__ __forceinline__ static float add(float a, float b) { return a + b; }
+  __device__ __forceinline__ static bool nz(float a) { return a != 0.0f; }
+  __device__ __forceinline__ static float rs(float a, double s) { return a * (float)s; }
+};
+template <>
 struct Num<cplx> {
   __device__ __forceinline__ static cplx zero() { return mkc(0.0, 0.0); }
   __device__ __forceinline__ static cplx cj(cplx a) { return cconj(a); }
@@ -258,9 +268,10 @@ static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
   gemm_kernel<T, BK><<<grid, 256, 0, s>>>(p);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
-  if (prof) prof_gemm_end(s, useful_macs(p) * (sizeof(T) == sizeof(cplx) ? 8.0 : 2.0));
+  if (prof) prof_gemm_end(s, sizeof(T) == sizeof(float) ? 0.0 : useful_macs(p) * (sizeof(T) == sizeof(cplx) ? 8.0 : 2.0));
   return BSE_OK;
 }
 
 bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) { return gemm_launch<cplx, 8>(s, p); }
 bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) { return gemm_launch<double, 16>(s, p); }
+bse_status gemm_f(cudaStream_t s, const GemmParams<float>& p) { return gemm_launch<float, 32>(s, p); }

@@ -57,6 +57,7 @@ GemmParams<T> gemm_params(int64_t m, int64_t n, int64_t k, int opA, const T* A, 
 
 bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p);
 bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p);
+bse_status gemm_f(cudaStream_t s, const GemmParams<float>& p);
 
 // Launch counter shared by all translation units.
 void bse_count_launch(int64_t k = 1);

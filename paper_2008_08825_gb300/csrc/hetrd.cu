@@ -21,8 +21,10 @@
 constexpr int NBT = 32;    // panel width
 constexpr int RB = 256;    // rows per CTA in column kernels
 constexpr int HCH = 512;   // column chunk of the Hermitian matvec
+constexpr int BTB = 128;   // reflectors per block in the back-transformation
 
 int hetrd_panel() { return NBT; }
+int backtransform_block() { return BTB; }
 static inline int64_t nchunks(int64_t m) { return (m + HCH - 1) / HCH; }
 size_t hetrd_part_elems(int64_t n) { return (size_t)(2 * nchunks(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64; }
 
@@ -144,16 +146,18 @@ __global__ void __launch_bounds__(RB) tr_hemv_lo(int64_t n, int64_t j, const cpl
   __syncthreads();
   if (r >= m) return;
   const int64_t cend = min(c1, r + 1);
-  cplx acc0 = mkc(0.0, 0.0), acc1 = mkc(0.0, 0.0);
+  cplx acc[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
   const cplx* Ar = A + IDX2(base + r, base, lda);
   int64_t c = c0;
-  for (; c + 1 < cend; c += 2) {
-    const cplx a0 = Ar[c * lda], a1 = Ar[(c + 1) * lda];
-    cfma(acc0, a0, vs[c - c0]);
-    cfma(acc1, a1, vs[c + 1 - c0]);
+  for (; c + 3 < cend; c += 4) {
+    cplx av[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ar + (c + u) * lda);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma(acc[u], av[u], vs[c + u - c0]);
   }
-  if (c < cend) cfma(acc0, Ar[c * lda], vs[c - c0]);
-  part[r + blockIdx.y * ldpart] = cadd(acc0, acc1);
+  for (; c < cend; ++c) cfma(acc[0], Ar[c * lda], vs[c - c0]);
+  part[r + blockIdx.y * ldpart] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
 // 3b. y2(c) = sum_{r > c} conj(A(r, c)) v(r), warp per column, partial over row chunks
@@ -171,9 +175,18 @@ __global__ void __launch_bounds__(RB) tr_hemv_up(int64_t n, int64_t j, const cpl
   for (int64_t rr = r0 + threadIdx.x; rr < r1; rr += RB) vs[rr - r0] = V[IDX2(base + rr, j, ldv)];
   __syncthreads();
   if (c >= m) return;
-  cplx acc = mkc(0.0, 0.0);
+  cplx accs[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
   const cplx* Ac = A + IDX2(base, base + c, lda);
-  for (int64_t rr = max(r0, c + 1) + lane; rr < r1; rr += 32) cfma_cj(acc, Ac[rr], vs[rr - r0]);
+  int64_t rr = max(r0, c + 1) + lane;
+  for (; rr + 96 < r1; rr += 128) {
+    cplx av[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ac + rr + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma_cj(accs[u], av[u], vs[rr + 32 * u - r0]);
+  }
+  for (; rr < r1; rr += 32) cfma_cj(accs[0], Ac[rr], vs[rr - r0]);
+  cplx acc = cadd(cadd(accs[0], accs[1]), cadd(accs[2], accs[3]));
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -355,7 +368,8 @@ bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cpl
   pg.status = status;
   bse_status r = gemm_z(s, pg);
   if (r) return r;
-  larft_kernel<<<1, 64, 0, s>>>((int)bs, G, (int)bs, tau + c0, T, (int)bs, status);
+  const int lt = (int)((bs + 31) / 32 * 32);
+  larft_kernel<<<1, lt, 0, s>>>((int)bs, G, (int)bs, tau + c0, T, (int)bs, status);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   GemmParams<cplx> p1 = gemm_params<cplx>(bs, k, m, OPC, Vp, ldvb, OPN, Vout + r0, ldv, one, zero, W1, bs);
@@ -373,10 +387,10 @@ bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cpl
 bse_status hetrd_backtransform(cudaStream_t s, int64_t n, int64_t k, const HetrdWork& w, cplx* Vout, int64_t ldv,
                                cplx* tmp, const int64_t* status) {
   if (n <= 1) return BSE_OK;
-  const int64_t npan = (n - 1 + NBT - 1) / NBT;
+  const int64_t npan = (n - 1 + BTB - 1) / BTB;
   for (int64_t b = npan - 1; b >= 0; --b) {
-    const int64_t p = b * NBT;
-    const int64_t bs = (n - 1 - p) < NBT ? (n - 1 - p) : NBT;
+    const int64_t p = b * BTB;
+    const int64_t bs = (n - 1 - p) < BTB ? (n - 1 - p) : BTB;
     bse_status r = apply_block_reflector(s, n, k, w.V, n, p, bs, p + 1, w.tau, Vout, ldv, tmp, status);
     if (r) return r;
   }

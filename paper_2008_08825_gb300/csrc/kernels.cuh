@@ -46,6 +46,8 @@ struct HetrdWork {
   cplx* small;    // small scratch (>= 4 * nbt * nbt + 64)
 };
 int hetrd_panel();
+// reflectors per block in the back-transformations (T factor of this width)
+int backtransform_block();
 size_t hetrd_part_elems(int64_t n);
 bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const HetrdWork& w,
                        const int64_t* status);
@@ -66,7 +68,8 @@ struct TriWork {
   int* iprm;       // 8 ints: number of blocks, ...
   double* scratch; // N * kmax doubles (twisted factorisation)
   double* E;       // kmax * kmax (orthogonalisation Gram matrix)
-  double* Z2;      // N * kmax doubles
+  float* Ef;       // kmax * kmax
+  double* Z2;      // N * kmax doubles (also holds two N * kmax float arrays)
 };
 // mode 0: all N eigenvalues of T.  mode 1 (Golub-Kahan form, zero diagonal,
 // even N): the N/2 positive eigenvalues (the upper half of each block).

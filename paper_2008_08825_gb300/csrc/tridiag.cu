@@ -14,9 +14,10 @@
 //    pivots, twist index r = argmin |gamma_r|): z_r = 1 and the two
 //    recurrences outward -- one step of inverse iteration from the best unit
 //    vector;
-//  * orthogonalisation: one Newton-Schulz step Z <- Z (3I - Z^T Z)/2 (two
-//    FP64 GEMMs) brings the O(eps ||T|| / gap) loss of orthogonality of close
-//    eigenvalues down to O(eps) without changing the residuals beyond O(eps ||T||).
+//  * orthogonalisation: one Newton-Schulz step Z <- Z (3I - Z^T Z)/2 (the
+//    Gram matrix in FP64, the small correction product in FP32) brings the
+//    O(eps ||T|| / gap) loss of orthogonality of close eigenvalues down to
+//    O(eps) without changing the residuals beyond O(eps ||T||).
 #include <float.h>
 
 #include "kernels.cuh"
@@ -212,22 +213,55 @@ __global__ void tri_vec_kernel(int64_t total, int64_t il, int64_t iu, const doub
   for (int k = 0; k < m; ++k) zc[k] *= inv;
 }
 
+// E (k x k, lower half computed) -> full symmetric, minus I, as float
+__global__ void ns_prep_kernel(int64_t k, const double* __restrict__ E, float* __restrict__ Ef) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= k || j >= k) return;
+  const double v = (i >= j) ? E[i + j * k] : E[j + i * k];
+  Ef[i + j * k] = (float)(v - (i == j ? 1.0 : 0.0));
+}
+
+__global__ void to_float_kernel(int64_t N, int64_t k, const double* __restrict__ Z, int64_t ldz, float* __restrict__ Zf) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < N && j < k) Zf[i + j * N] = (float)Z[i + j * ldz];
+}
+
+__global__ void ns_update_kernel(int64_t N, int64_t k, double* __restrict__ Z, int64_t ldz, const float* __restrict__ D) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < N && j < k) Z[i + j * ldz] -= 0.5 * (double)D[i + j * N];
+}
+
+// One Newton-Schulz step Z <- Z - Z E / 2 with E = Z^T Z - I.  E needs FP64
+// (its entries are O(eps ||T|| / gap) and come from cancellation), only its
+// lower half is computed; the product Z E is O(|E|) and needs only ~7 digits,
+// so it runs in FP32 (FFMA), its rounding error O(1e-7 |E|) being far below
+// FP64 rounding of Z.
 bse_status orthonormalize_columns(cudaStream_t s, int64_t N, int64_t k, double* Z, int64_t ldz, const TriWork& w,
                                   const int64_t* status) {
   if (k <= 0 || N <= 0) return BSE_OK;
-  // E = Z^T Z - I;  Z <- Z - 0.5 Z E
   GemmParams<double> pe = gemm_params<double>(k, k, N, OPT, Z, ldz, OPN, Z, ldz, 1.0, 0.0, w.E, k);
+  pe.lowerC = 1;
   pe.status = status;
   bse_status r = gemm_d(s, pe);
   if (r) return r;
-  if ((r = sub_identity(s, k, w.E, k))) return r;
-  BSE_CUDA(cudaMemcpy2DAsync(w.Z2, sizeof(double) * N, Z, sizeof(double) * ldz, sizeof(double) * N, k,
-                             cudaMemcpyDeviceToDevice, s));
-  GemmParams<double> pz = gemm_params<double>(N, k, k, OPN, Z, ldz, OPN, w.E, k, -0.5, 1.0, w.Z2, N);
+  float* Zf = (float*)w.Z2;
+  float* D = Zf + N * k;
+  dim3 gk(ceil_div_u(k, 256), (unsigned)k), gn(ceil_div_u(N, 256), (unsigned)k);
+  ns_prep_kernel<<<gk, 256, 0, s>>>(k, w.E, w.Ef);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  to_float_kernel<<<gn, 256, 0, s>>>(N, k, Z, ldz, Zf);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  GemmParams<float> pz = gemm_params<float>(N, k, k, OPN, Zf, N, OPN, w.Ef, k, 1.0f, 0.0f, D, N);
   pz.status = status;
-  if ((r = gemm_d(s, pz))) return r;
-  BSE_CUDA(cudaMemcpy2DAsync(Z, sizeof(double) * ldz, w.Z2, sizeof(double) * N, sizeof(double) * N, k,
-                             cudaMemcpyDeviceToDevice, s));
+  if ((r = gemm_f(s, pz))) return r;
+  ns_update_kernel<<<gn, 256, 0, s>>>(N, k, Z, ldz, D);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
 

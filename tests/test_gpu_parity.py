@@ -195,7 +195,7 @@ def test_kappa_sweep_vs_oracle(kappa, method, dev):
     else:
         # CHOL computes omega^2 = eig(L^H (A+B) L), whose absolute error is
         # O(eps ||H||^2); Eq. (SquaredErr) turns it into |d omega_i| ~ eps ||H||^2 / omega_i
-        tol = 64 * np.finfo(float).eps * om_r.max() ** 2 / om_r
+        tol = np.maximum(1e-11 * om_r.max(), 64 * np.finfo(float).eps * om_r.max() ** 2 / om_r)
         assert np.all(np.abs(om - om_r) <= tol)
     rel_small = abs(om[0] - om_r[0]) / om_r[0]
     print(f"kappa={kappa:g} method={method} rel.err(smallest)={rel_small:.2e} sigma={sigma_residual(X, Y):.2e}")
