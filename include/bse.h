@@ -143,6 +143,41 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
                           double* omega, double* X, int64_t ldx, double* Y, int64_t ldy,
                           bse_info* info, void* stream);
 
+/*
+ * Batched Cholesky method (Alg. 2 for each instance): `count` independent
+ * problems of sizes n[i] (1 <= n[i] <= 1024), the k lowest eigenpairs of each
+ * (k_i = min(k, n[i])), in ONE persistent kernel launch: each CTA takes the
+ * next instance from a queue ordered by decreasing n and solves it alone.
+ * n        host array, count sizes.
+ * A, B     host arrays of count DEVICE pointers; instance i is n[i] x n[i]
+ *          Hermitian with leading dimension n[i] (lower triangle read).
+ * omega    host array of count device pointers to k_i doubles (ascending).
+ * X, Y     host arrays of count device pointers to n[i] x k_i complex
+ *          matrices, leading dimension n[i].
+ * status   host array of count int64 (may be NULL): 0 or the instance's
+ *          bse_status code.  The return value is BSE_OK when every instance
+ *          succeeded, else the first failing instance's code.
+ * method   BSE_METHOD_CHOL (BSE_METHOD_SVD returns BSE_ERR_NOT_IMPLEMENTED);
+ * prec     BSE_PREC_FP64.
+ */
+bse_status bse_solve_batched(bse_handle h, int64_t count, const int64_t* n, const double* const* A,
+                             const double* const* B, int64_t k, int method, int prec, double* const* omega,
+                             double* const* X, double* const* Y, int64_t* status, void* stream);
+
+/*
+ * Enqueue-only form of bse_solve_batched, for CUDA-graph capture: copies
+ * the instance table from library-owned pinned host memory, resets the
+ * queue, launches the persistent kernel and returns without synchronising.
+ * dstatus  DEVICE array of 2*count int64 written by the kernel (code, info
+ *          per instance); read it after synchronising the stream.
+ * The pointer arrays must describe the same sizes on every replay of a
+ * captured graph (the table is rebuilt at capture time).
+ */
+bse_status bse_solve_batched_async(bse_handle h, int64_t count, const int64_t* n, const double* const* A,
+                                   const double* const* B, int64_t k, int method, int prec,
+                                   double* const* omega, double* const* X, double* const* Y,
+                                   int64_t* dstatus, void* stream);
+
 /* Number of CUDA kernel launches the library has issued so far in this
  * process (all handles, all entry points). */
 int64_t bse_launch_count(bse_handle h);

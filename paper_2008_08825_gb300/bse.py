@@ -78,6 +78,9 @@ def _bind(lib):
                                    _I64, _P, _I64, ctypes.POINTER(_Info), _P]
     lib.bse_launch_count.argtypes = [_P]
     lib.bse_launch_count.restype = ctypes.c_int64
+    for f in (lib.bse_solve_batched, lib.bse_solve_batched_async):
+        f.argtypes = [_P, _I64, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
+        f.restype = ctypes.c_int
     lib.bse_profile_enable.argtypes = [_P, ctypes.c_int]
     lib.bse_profile_enable.restype = ctypes.c_int
     lib.bse_profile_read.restype = ctypes.c_int
@@ -274,3 +277,57 @@ class Omega(torch.autograd.Function):
         Ys = Ys.mT.contiguous().mT
         dA, dB = grad(Xs, Ys, g)
         return dA, dB, None, None
+
+
+class Batch:
+    """Device buffers and pointer tables of a batched solve (the k lowest pairs
+    of many instances, Alg. 2 each, one persistent launch).
+
+    instances: list of (A, B) complex128 CUDA tensors (n_i x n_i, n_i <= 1024).
+    """
+
+    def __init__(self, instances, k: int = 32):
+        self.count = len(instances)
+        self.k = int(k)
+        dev = instances[0][0].device if instances else torch.device("cuda")
+        self.n = [int(A.shape[0]) for A, _ in instances]
+        self.A = [_colmajor(A) for A, _ in instances]
+        self.B = [_colmajor(B) for _, B in instances]
+        self.ks = [min(self.k, n) for n in self.n]
+        self.omega = [torch.empty(k_i, dtype=torch.float64, device=dev) for k_i in self.ks]
+        self.Xt = [torch.empty((k_i, n), dtype=torch.complex128, device=dev) for n, k_i in zip(self.n, self.ks)]
+        self.Yt = [torch.empty((k_i, n), dtype=torch.complex128, device=dev) for n, k_i in zip(self.n, self.ks)]
+        self.dstatus = torch.zeros(2 * max(self.count, 1), dtype=torch.int64, device=dev)
+
+        def arr(ctype, vals):
+            return (ctype * max(len(vals), 1))(*vals)
+
+        self._n = arr(ctypes.c_int64, self.n)
+        self._A = arr(ctypes.c_void_p, [t.data_ptr() for t in self.A])
+        self._B = arr(ctypes.c_void_p, [t.data_ptr() for t in self.B])
+        self._om = arr(ctypes.c_void_p, [t.data_ptr() for t in self.omega])
+        self._X = arr(ctypes.c_void_p, [t.data_ptr() for t in self.Xt])
+        self._Y = arr(ctypes.c_void_p, [t.data_ptr() for t in self.Yt])
+
+    def _args(self):
+        return (self.count, self._n, self._A, self._B, self.k, 0, 0, self._om, self._X, self._Y)
+
+    def run(self, handle: Handle | None = None, stream=None):
+        """Synchronous solve; raises on the first failing instance."""
+        h = handle or default_handle()
+        st = (ctypes.c_int64 * max(self.count, 1))()
+        code = lib().bse_solve_batched(h.ptr, *self._args(), st, _P(_stream_ptr(stream)))
+        self.status = list(st)[: self.count]
+        _check(code)
+        return self
+
+    def enqueue(self, handle: Handle | None = None, stream=None):
+        """Enqueue only (capturable in a CUDA graph); statuses land in self.dstatus."""
+        h = handle or default_handle()
+        code = lib().bse_solve_batched_async(h.ptr, *self._args(), _P(self.dstatus.data_ptr()),
+                                             _P(_stream_ptr(stream)))
+        _check(code)
+        return self
+
+    def results(self):
+        return [(o, X.mT, Y.mT) for o, X, Y in zip(self.omega, self.Xt, self.Yt)]

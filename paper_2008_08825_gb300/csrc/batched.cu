@@ -1,0 +1,498 @@
+// Batched solver: many independent BSE instances of uneven size n <= 1024,
+// the lowest k eigenpairs of each, in ONE persistent launch (Alg. 2 per
+// instance).  Each CTA pops the next instance from a queue sorted by size
+// (largest first, so the long ones start first) and runs the whole Cholesky
+// pipeline for it with CTA-local routines:
+//   form M1 = A + B, M2 = A - B; blocked Cholesky of M2 (block 32, the
+//   GEMM engine's tile routine for the panel and the trailing update);
+//   W = M1 L, M = L^H W (tile routine); unblocked Householder
+//   tridiagonalisation of M (lower storage, explicit reflectors kept in M);
+//   bisection for the k smallest eigenvalues of T; twisted-factorisation
+//   vectors; one Newton-Schulz step; back-transformation one reflector at a
+//   time (a warp per column, no barriers); P = L^{-H} V_M by column-wise
+//   substitution; X, Y from P and L V_M through the tile routine's fused
+//   epilogue (Alg. 2 steps 4-6).
+// A whole instance stays on one SM, so nothing synchronises across CTAs;
+// the only global atomic is the queue counter.
+#include <float.h>
+
+#include "gemm_tile.cuh"
+#include "kernels.cuh"
+
+constexpr int BT = 256;       // threads per CTA
+constexpr int CNB = 32;       // Cholesky block
+constexpr int CLD = CNB + 1;
+
+struct BatchDesc {
+  int64_t n, k;
+  const cplx* A;
+  const cplx* B;
+  double* omega;
+  cplx* X;
+  cplx* Y;
+  char* ws;
+  int64_t* status;  // code, info
+};
+
+struct InstWs {
+  cplx *M1, *L, *W, *Linv, *tau, *VM, *P;
+  double *d, *e, *e2, *Z, *sc, *E, *lam, *c1, *c2;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__host__ __device__ inline size_t carve_inst(char* base, int64_t n, int64_t k, InstWs* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = align256(off);
+    char* p = base ? base + off : nullptr;
+    off += bytes > 0 ? bytes : 1;
+    return p;
+  };
+  const size_t nn = (size_t)n * n, nk = (size_t)n * k;
+  InstWs t;
+  t.M1 = (cplx*)take(nn * 16);
+  t.L = (cplx*)take(nn * 16);
+  t.W = (cplx*)take(nn * 16);
+  t.Linv = (cplx*)take(CNB * CNB * 16);
+  t.tau = (cplx*)take(n * 16);
+  t.VM = (cplx*)take(nk * 16);
+  t.P = (cplx*)take(nk * 16);
+  t.d = (double*)take(n * 8);
+  t.e = (double*)take(n * 8);
+  t.e2 = (double*)take(n * 8);
+  t.Z = (double*)take(nk * 8);
+  t.sc = (double*)take(nk * 8);
+  t.E = (double*)take((size_t)k * k * 8);
+  t.lam = (double*)take(k * 8);
+  t.c1 = (double*)take(k * 8);
+  t.c2 = (double*)take(k * 8);
+  if (w) *w = t;
+  return align256(off);
+}
+
+size_t batched_inst_bytes(int64_t n, int64_t k) { return carve_inst(nullptr, n, k, nullptr); }
+int batched_max_n() { return 1024; }
+
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < BT / 32; ++w) t += red[w];
+  __syncthreads();
+  return t;  // every thread gets the same value
+}
+
+__device__ __forceinline__ double cta_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = red[0];
+  for (int w = 1; w < BT / 32; ++w) t = fmax(t, red[w]);
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double cta_min(double v, double* red) { return -cta_max(-v, red); }
+
+// ---- Cholesky of the lower triangle of L (n x n, ld n), block CNB ----------
+__device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx* S, cplx* Iv, int* flag) {
+  const int tid = threadIdx.x;
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), mone = mkc(-1.0, 0.0);
+  for (int64_t k0 = 0; k0 < n; k0 += CNB) {
+    const int bs = (int)((n - k0) < CNB ? (n - k0) : CNB);
+    for (int e = tid; e < CNB * CNB; e += BT) {
+      const int i = e % CNB, j = e / CNB;
+      S[i + j * CLD] = (i < bs && j < bs && i >= j) ? L[IDX2(k0 + i, k0 + j, n)] : zero;
+      Iv[i + j * CLD] = zero;
+    }
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    for (int j = 0; j < bs; ++j) {
+      if (tid == 0) {
+        const double dd = S[j + j * CLD].x;
+        if (!(dd > 0.0)) {
+          *flag = 1;
+          status[0] = BSE_ERR_NOT_PD_AMINUSB;
+          status[1] = k0 + j + 1;
+        } else {
+          S[j + j * CLD] = mkc(sqrt(dd), 0.0);
+        }
+      }
+      __syncthreads();
+      if (*flag) return false;
+      const double rl = 1.0 / S[j + j * CLD].x;
+      for (int i = j + 1 + tid; i < bs; i += BT) S[i + j * CLD] = cscale(S[i + j * CLD], rl);
+      __syncthreads();
+      const int m = bs - j - 1;
+      for (int e = tid; e < m * m; e += BT) {
+        const int ii = e % m, kc = e / m;
+        if (ii < kc) continue;
+        const int i = j + 1 + ii, c = j + 1 + kc;
+        const cplx a = S[i + j * CLD], b = S[c + j * CLD];
+        cplx v = S[i + c * CLD];
+        v.x -= a.x * b.x + a.y * b.y;
+        v.y -= a.y * b.x - a.x * b.y;
+        S[i + c * CLD] = v;
+      }
+      __syncthreads();
+    }
+    if (tid < bs) {
+      const int c = tid;
+      Iv[c + c * CLD] = mkc(1.0 / S[c + c * CLD].x, 0.0);
+      for (int i = c + 1; i < bs; ++i) {
+        cplx s = zero;
+        for (int kk = c; kk < i; ++kk) cfma(s, S[i + kk * CLD], Iv[kk + c * CLD]);
+        Iv[i + c * CLD] = cscale(s, -1.0 / S[i + i * CLD].x);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < bs * bs; e += BT) {
+      const int i = e % bs, j = e / bs;
+      L[IDX2(k0 + i, k0 + j, n)] = (i >= j) ? S[i + j * CLD] : zero;
+      Linv[i + j * CNB] = (i >= j) ? Iv[i + j * CLD] : zero;
+    }
+    __threadfence_block();
+    __syncthreads();
+    const int64_t m2 = n - k0 - bs;
+    if (m2 <= 0) continue;
+    cplx* A21 = L + IDX2(k0 + bs, k0, n);
+    cplx* A22 = L + IDX2(k0 + bs, k0 + bs, n);
+    GemmParams<cplx> p = gemm_params<cplx>(m2, bs, bs, OPN, A21, n, OPC, Linv, CNB, one, zero, A21, n);
+    p.triB = TRI_UP;
+    gemm_cta<cplx, 8>(p);
+    __threadfence_block();
+    GemmParams<cplx> q = gemm_params<cplx>(m2, m2, bs, OPN, A21, n, OPC, A21, n, mone, one, A22, n);
+    q.lowerC = 1;
+    gemm_cta<cplx, 8>(q);
+    __threadfence_block();
+    __syncthreads();
+  }
+  return true;
+}
+
+// ---- unblocked Householder tridiagonalisation of the lower triangle of M ----
+// Reflector j is stored explicitly in M(j+1:, j) (unit first entry).
+__device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, cplx* vs, cplx* ws, double* red) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ cplx h_tau, h_scal, h_alpha;
+  __shared__ double h_beta;
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    const int64_t base = j + 1, m = n - base;
+    double nrm = 0.0;
+    for (int64_t r = 2 + tid; r < m + 1; r += BT) nrm += cabs2(M[IDX2(j + r, j, n)]);  // rows j+2..n-1
+    nrm = cta_sum(nrm, red);
+    if (tid == 0) {
+      const cplx alpha = M[IDX2(base, j, n)];
+      d[j] = M[IDX2(j, j, n)].x;
+      if (nrm == 0.0 && alpha.y == 0.0) {
+        h_tau = mkc(0.0, 0.0);
+        h_beta = alpha.x;
+        h_scal = mkc(0.0, 0.0);
+      } else {
+        const double nr = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + nrm);
+        const double beta = (alpha.x >= 0.0) ? -nr : nr;
+        h_beta = beta;
+        h_tau = mkc((beta - alpha.x) / beta, -alpha.y / beta);
+        h_scal = cdiv(mkc(1.0, 0.0), mkc(alpha.x - beta, alpha.y));
+      }
+      tau[j] = h_tau;
+      e[j] = h_beta;
+    }
+    __syncthreads();
+    for (int64_t r = tid; r < m; r += BT) {
+      const cplx v = (r == 0) ? mkc(1.0, 0.0) : cmul(M[IDX2(base + r, j, n)], h_scal);
+      vs[r] = v;
+      M[IDX2(base + r, j, n)] = v;
+    }
+    __syncthreads();
+    // w = A22 v: lower part (c <= r) by rows, strict upper by columns
+    for (int64_t r = tid; r < m; r += BT) {
+      cplx acc0 = mkc(0.0, 0.0), acc1 = mkc(0.0, 0.0);
+      const cplx* Ar = M + IDX2(base + r, base, n);
+      int64_t c = 0;
+      for (; c + 1 <= r; c += 2) {
+        cfma(acc0, Ar[c * n], vs[c]);
+        cfma(acc1, Ar[(c + 1) * n], vs[c + 1]);
+      }
+      if (c <= r) cfma(acc0, Ar[c * n], vs[c]);
+      const cplx* Ac = M + IDX2(base, base + r, n);
+      for (int64_t rr = r + 1; rr < m; ++rr) cfma_cj(acc1, Ac[rr], vs[rr]);
+      ws[r] = cmul(h_tau, cadd(acc0, acc1));
+    }
+    __syncthreads();
+    double dre = 0.0, dim = 0.0;
+    for (int64_t r = tid; r < m; r += BT) {
+      const cplx t = cmul(cconj(ws[r]), vs[r]);
+      dre += t.x, dim += t.y;
+    }
+    dre = cta_sum(dre, red);
+    dim = cta_sum(dim, red);
+    if (tid == 0) h_alpha = cscale(cmul(h_tau, mkc(dre, dim)), -0.5);
+    __syncthreads();
+    for (int64_t r = tid; r < m; r += BT) ws[r] = cadd(ws[r], cmul(h_alpha, vs[r]));
+    __syncthreads();
+    // A22 -= v w^H + w v^H (lower): warp per column, lanes over rows
+    for (int64_t c = warp; c < m; c += BT / 32) {
+      const cplx wc = cconj(ws[c]), vc = cconj(vs[c]);
+      cplx* Acol = M + IDX2(base, base + c, n);
+      for (int64_t r = c + lane; r < m; r += 32) {
+        cplx a = Acol[r];
+        a = csub(a, cadd(cmul(vs[r], wc), cmul(ws[r], vc)));
+        if (r == c) a.y = 0.0;
+        Acol[r] = a;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) d[n - 1] = M[IDX2(n - 1, n - 1, n)].x;
+  __syncthreads();
+}
+
+__device__ __forceinline__ int bsturm(const double* a, const double* e2, int64_t n, double x, double pivmin) {
+  double q = a[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = q < 0.0;
+  for (int64_t i = 1; i < n; ++i) {
+    q = (a[i] - x) - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+// ---- the whole instance -----------------------------------------------------
+__device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* red, cplx* S, cplx* Iv, int* flag) {
+  const int64_t n = D.n, k = D.k;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  InstWs w;
+  carve_inst(D.ws, n, k, &w);
+  int64_t* st = D.status;
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  // form M1 (full) and M2 (lower, into L)
+  for (int64_t q = tid; q < n * n; q += BT) {
+    const int64_t i = q % n, j = q / n;
+    if (i >= j) {
+      const cplx a = D.A[IDX2(i, j, n)], b = D.B[IDX2(i, j, n)];
+      w.M1[q] = (i == j) ? mkc(a.x + b.x, 0.0) : cadd(a, b);
+      w.L[q] = (i == j) ? mkc(a.x - b.x, 0.0) : csub(a, b);
+    } else {
+      const cplx a = D.A[IDX2(j, i, n)], b = D.B[IDX2(j, i, n)];
+      w.M1[q] = cconj(cadd(a, b));
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (!cta_potrf(n, w.L, w.Linv, st, S, Iv, flag)) return;
+  // W = M1 L ; M = L^H W (lower) into M1
+  GemmParams<cplx> p1 = gemm_params<cplx>(n, n, n, OPN, w.M1, n, OPN, w.L, n, one, zero, w.W, n);
+  p1.triB = TRI_LO;
+  gemm_cta<cplx, 8>(p1);
+  __threadfence_block();
+  __syncthreads();
+  GemmParams<cplx> p2 = gemm_params<cplx>(n, n, n, OPC, w.L, n, OPN, w.W, n, one, zero, w.M1, n);
+  p2.triA = TRI_UP;
+  p2.lowerC = 1;
+  gemm_cta<cplx, 8>(p2);
+  __threadfence_block();
+  __syncthreads();
+  cta_hetrd(n, w.M1, w.tau, w.d, w.e, vs, wsv, red);
+  // tridiagonal: bounds, bisection for the k smallest
+  double tn = 0.0, em = 0.0, lo = 1e308, hi = -1e308;
+  for (int64_t i = tid; i < n; i += BT) {
+    const double ol = i > 0 ? fabs(w.e[i - 1]) : 0.0, orr = i < n - 1 ? fabs(w.e[i]) : 0.0;
+    tn = fmax(tn, fabs(w.d[i]) + ol + orr);
+    lo = fmin(lo, w.d[i] - ol - orr);
+    hi = fmax(hi, w.d[i] + ol + orr);
+    if (i < n - 1) {
+      w.e2[i] = w.e[i] * w.e[i];
+      em = fmax(em, w.e2[i]);
+    }
+  }
+  tn = cta_max(tn, red);
+  em = cta_max(em, red);
+  lo = cta_min(lo, red);
+  hi = cta_max(hi, red);
+  __threadfence_block();
+  __syncthreads();
+  const double pivmin = DBL_MIN * fmax(1.0, em), g = DBL_EPSILON * fmax(tn, DBL_MIN);
+  lo -= 2.0 * DBL_EPSILON * tn + 4.0 * pivmin;
+  hi += 2.0 * DBL_EPSILON * tn + 4.0 * pivmin;
+  for (int64_t t = tid; t < k; t += BT) {
+    double a = lo, b = hi;
+    for (int it = 0; it < 256; ++it) {
+      const double mid = 0.5 * (a + b), wd = b - a;
+      if (wd <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)) || wd <= 4.0 * pivmin || mid == a || mid == b) break;
+      if (bsturm(w.d, w.e2, n, mid, pivmin) > t) b = mid; else a = mid;
+    }
+    const double l = 0.5 * (a + b);
+    w.lam[t] = l;
+    // twisted factorisation vector into Z(:, t)
+    double* zc = w.Z + t * n;
+    double* sc = w.sc + t * n;
+    double x = w.d[0] - l;
+    if (fabs(x) < g) x = (x < 0.0) ? -g : g;
+    zc[0] = x;
+    for (int64_t i = 1; i < n; ++i) {
+      x = (w.d[i] - l) - w.e2[i - 1] / x;
+      if (fabs(x) < g) x = (x < 0.0) ? -g : g;
+      zc[i] = x;
+    }
+    double y = w.d[n - 1] - l;
+    if (fabs(y) < g) y = (y < 0.0) ? -g : g;
+    sc[n - 1] = y;
+    double best = fabs(zc[n - 1]);
+    int64_t r = n - 1;
+    for (int64_t i = n - 2; i >= 0; --i) {
+      const double ai = w.d[i] - l;
+      y = ai - w.e2[i] / y;
+      if (fabs(y) < g) y = (y < 0.0) ? -g : g;
+      sc[i] = y;
+      const double gam = zc[i] + y - ai;
+      if (fabs(gam) < best) best = fabs(gam), r = i;
+    }
+    double nrm2 = 1.0, z = 1.0;
+    for (int64_t i = r - 1; i >= 0; --i) {
+      z = -(w.e[i] / zc[i]) * z;
+      zc[i] = z;
+      nrm2 += z * z;
+    }
+    zc[r] = 1.0;
+    z = 1.0;
+    for (int64_t i = r; i < n - 1; ++i) {
+      z = -(w.e[i] / sc[i + 1]) * z;
+      zc[i + 1] = z;
+      nrm2 += z * z;
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int64_t i = 0; i < n; ++i) zc[i] *= inv;
+    if (!(l > 0.0)) {
+      st[0] = BSE_ERR_NOT_PD_APLUSB;
+      st[1] = 0;
+    }
+    const double om = sqrt(l);
+    D.omega[t] = om;
+    w.c1[t] = sqrt(om);
+    w.c2[t] = 1.0 / sqrt(om);
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (st[0]) return;
+  // Newton-Schulz: E = Z^T Z - I, Z <- Z - Z E / 2 (k x k small, plain loops)
+  for (int64_t q = tid; q < k * k; q += BT) {
+    const int64_t a = q % k, b = q / k;
+    if (a < b) continue;
+    const double* za = w.Z + a * n;
+    const double* zb = w.Z + b * n;
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = fma(za[i], zb[i], s);
+    if (a == b) s -= 1.0;
+    w.E[a + b * k] = s;
+    w.E[b + a * k] = s;
+  }
+  __threadfence_block();
+  __syncthreads();
+  for (int64_t q = tid; q < n * k; q += BT) {
+    const int64_t i = q % n, c = q / n;
+    double s = 0.0;
+    for (int64_t b = 0; b < k; ++b) s = fma(w.Z[i + b * n], w.E[b + c * k], s);
+    w.sc[q] = w.Z[q] - 0.5 * s;
+  }
+  __threadfence_block();
+  __syncthreads();
+  for (int64_t q = tid; q < n * k; q += BT) w.VM[q] = mkc(w.sc[q], 0.0);
+  __threadfence_block();
+  __syncthreads();
+  // V_M = H_0 ... H_{n-2} Z, one reflector at a time; a warp owns columns
+  for (int64_t c = warp; c < k; c += BT / 32) {
+    cplx* vc = w.VM + c * n;
+    for (int64_t j = n - 2; j >= 0; --j) {
+      const cplx* v = w.M1 + IDX2(j + 1, j, n);
+      const int64_t m = n - j - 1;
+      cplx s = mkc(0.0, 0.0);
+      for (int64_t r = lane; r < m; r += 32) cfma_cj(s, v[r], vc[j + 1 + r]);
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      const cplx ts = cmul(w.tau[j], s);
+      for (int64_t r = lane; r < m; r += 32) vc[j + 1 + r] = csub(vc[j + 1 + r], cmul(v[r], ts));
+      __syncwarp();
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  // P = L^{-H} V_M, column by column (a warp owns a column)
+  for (int64_t c = warp; c < k; c += BT / 32) {
+    const cplx* vmc = w.VM + c * n;
+    cplx* pc = w.P + c * n;
+    for (int64_t i = n - 1; i >= 0; --i) {
+      const cplx* li = w.L + IDX2(0, i, n);
+      cplx s = mkc(0.0, 0.0);
+      for (int64_t r = i + 1 + lane; r < n; r += 32) cfma_cj(s, li[r], pc[r]);
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) pc[i] = cscale(csub(vmc[i], s), 1.0 / li[i].x);
+      __syncwarp();
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  // X, Y: v2 = L V_M, X = (c1 P + c2 v2)/2, Y = (c2 v2 - c1 P)/2
+  GemmParams<cplx> p3 = gemm_params<cplx>(n, k, n, OPN, w.L, n, OPN, w.VM, n, one, zero, D.X, n);
+  p3.triA = TRI_LO;
+  p3.epi = EPI_XY;
+  p3.P = w.P, p3.ldp = n, p3.c1 = w.c1, p3.c2 = w.c2, p3.Y = D.Y, p3.ldy = n;
+  gemm_cta<cplx, 8>(p3);
+}
+
+__global__ void __launch_bounds__(BT, 2) batched_chol_kernel(const BatchDesc* __restrict__ desc, int64_t count,
+                                                             int* counter) {
+  extern __shared__ cplx dyn[];
+  cplx* vs = dyn;                    // 1024
+  cplx* wsv = dyn + 1024;            // 1024
+  cplx* S = dyn + 2048;              // CNB x CLD
+  cplx* Iv = S + CNB * CLD;          // CNB x CLD
+  __shared__ double red[BT / 32];
+  __shared__ int next, flag;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = next;
+    __syncthreads();
+    if (idx >= count) break;
+    solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag);
+    __syncthreads();
+  }
+}
+
+size_t batched_smem_bytes() { return sizeof(cplx) * (2048 + 2 * CNB * CLD); }
+
+bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid) {
+  static bool attr = false;
+  const size_t smem = batched_smem_bytes();
+  if (!attr) {
+    BSE_CUDA(cudaFuncSetAttribute(batched_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  BSE_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  batched_chol_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+size_t batched_desc_bytes() { return sizeof(BatchDesc); }
+
+void batched_fill_desc(void* slot, int64_t n, int64_t k, const void* A, const void* B, double* omega, void* X, void* Y,
+                       char* ws, int64_t* status) {
+  BatchDesc d;
+  d.n = n, d.k = k, d.A = (const cplx*)A, d.B = (const cplx*)B, d.omega = omega, d.X = (cplx*)X, d.Y = (cplx*)Y;
+  d.ws = ws, d.status = status;
+  *(BatchDesc*)slot = d;
+}

@@ -22,6 +22,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -43,6 +44,11 @@ struct bse_context {
   int64_t* host_status = nullptr;  // pinned, 2 entries
   Profiler* prof = nullptr;
   int prof_on = 0;
+  void* bws = nullptr;       // batched workspace
+  size_t bws_bytes = 0;
+  char* bdesc_host = nullptr;  // pinned instance table
+  size_t bdesc_bytes = 0;
+  int sms = 0;
 };
 
 // Makes the handle's profiler current for this thread for one entry point;
@@ -405,6 +411,107 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
   return finish(h, s, st, info);
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched solves.
+static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* n, const double* const* A,
+                                  const double* const* B, int64_t k, int method, int prec, double* const* omega,
+                                  double* const* X, double* const* Y, int64_t** dstatus_out, int64_t* dstatus_user,
+                                  cudaStream_t s) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  if (count < 0 || k < 1) return bse_internal_set_error("count < 0 or k < 1"), BSE_ERR_ARG;
+  if (method == BSE_METHOD_SVD) return bse_internal_set_error("batched SVD method is not available in this build"), BSE_ERR_NOT_IMPLEMENTED;
+  if (method != BSE_METHOD_CHOL) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
+  if (prec != BSE_PREC_FP64) return bse_internal_set_error("batched solves are FP64 only"), BSE_ERR_NOT_IMPLEMENTED;
+  if (count == 0) return BSE_OK;
+  if (!n || !A || !B || !omega || !X || !Y) return bse_internal_set_error("NULL array"), BSE_ERR_ARG;
+  for (int64_t i = 0; i < count; ++i) {
+    if (n[i] < 1 || n[i] > batched_max_n()) return bse_internal_set_error("batched n out of [1, 1024]"), BSE_ERR_ARG;
+    if (!A[i] || !B[i] || !omega[i] || !X[i] || !Y[i]) return bse_internal_set_error("NULL instance pointer"), BSE_ERR_ARG;
+  }
+  // largest first (longest-processing-time order for the persistent queue)
+  std::vector<int64_t> order(count);
+  for (int64_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return n[a] > n[b]; });
+  size_t ws_total = 0;
+  std::vector<size_t> offs(count);
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t i = order[q];
+    offs[q] = ws_total;
+    ws_total += batched_inst_bytes(n[i], k < n[i] ? k : n[i]);
+  }
+  const size_t desc_bytes = (batched_desc_bytes() * count + 255) & ~(size_t)255;
+  const size_t stat_bytes = ((size_t)16 * count + 255) & ~(size_t)255;
+  const size_t need = ws_total + desc_bytes + stat_bytes + 256;
+  if (h->bws_bytes < need) {
+    if (h->bws) cudaFree(h->bws);
+    h->bws = nullptr;
+    h->bws_bytes = 0;
+    if (cudaMalloc(&h->bws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return bse_internal_set_error("cudaMalloc of batched workspace failed"), BSE_ERR_NOMEM;
+    }
+    h->bws_bytes = need;
+  }
+  if (h->bdesc_bytes < desc_bytes) {
+    if (h->bdesc_host) cudaFreeHost(h->bdesc_host);
+    h->bdesc_host = nullptr;
+    h->bdesc_bytes = 0;
+    if (cudaMallocHost(&h->bdesc_host, desc_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return bse_internal_set_error("cudaMallocHost of the instance table failed"), BSE_ERR_NOMEM;
+    }
+    h->bdesc_bytes = desc_bytes;
+  }
+  char* base = (char*)h->bws;
+  char* ddesc = base + ws_total;
+  int64_t* dstat = dstatus_user ? dstatus_user : (int64_t*)(ddesc + desc_bytes);
+  int* counter = (int*)(ddesc + desc_bytes + stat_bytes);
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t i = order[q];
+    batched_fill_desc(h->bdesc_host + q * batched_desc_bytes(), n[i], k < n[i] ? k : n[i], A[i], B[i], omega[i],
+                      X[i], Y[i], base + offs[q], dstat + 2 * i);
+  }
+  BSE_CUDA(cudaMemcpyAsync(ddesc, h->bdesc_host, batched_desc_bytes() * count, cudaMemcpyHostToDevice, s));
+  BSE_CUDA(cudaMemsetAsync(dstat, 0, 16 * count, s));
+  const int grid = (int)std::min<int64_t>(count, (int64_t)h->sms * 2);
+  TRY(batched_chol_launch(s, ddesc, count, counter, grid));
+  if (dstatus_out) *dstatus_out = dstat;
+  return BSE_OK;
+}
+
+extern "C" bse_status bse_solve_batched_async(bse_handle h, int64_t count, const int64_t* n, const double* const* A,
+                                              const double* const* B, int64_t k, int method, int prec,
+                                              double* const* omega, double* const* X, double* const* Y,
+                                              int64_t* dstatus, void* stream) {
+  if (!dstatus && count > 0) return bse_internal_set_error("NULL dstatus"), BSE_ERR_ARG;
+  return batched_enqueue(h, count, n, A, B, k, method, prec, omega, X, Y, nullptr, dstatus, (cudaStream_t)stream);
+}
+
+extern "C" bse_status bse_solve_batched(bse_handle h, int64_t count, const int64_t* n, const double* const* A,
+                                        const double* const* B, int64_t k, int method, int prec, double* const* omega,
+                                        double* const* X, double* const* Y, int64_t* status, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t* dstat = nullptr;
+  TRY(batched_enqueue(h, count, n, A, B, k, method, prec, omega, X, Y, &dstat, nullptr, s));
+  if (count == 0) return BSE_OK;
+  std::vector<int64_t> hs(2 * count);
+  BSE_CUDA(cudaMemcpyAsync(hs.data(), dstat, 16 * count, cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  bse_status first = BSE_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    if (status) status[i] = hs[2 * i];
+    if (hs[2 * i] != 0 && first == BSE_OK) {
+      first = (bse_status)hs[2 * i];
+      char buf[128];
+      snprintf(buf, sizeof buf, "batched instance %lld: status %lld (info %lld)", (long long)i, (long long)hs[2 * i],
+               (long long)hs[2 * i + 1]);
+      bse_internal_set_error(buf);
+    }
+  }
+  return first;
+}
+
 // ---------------------------------------------------------------------------
 extern "C" {
 
@@ -418,6 +525,7 @@ bse_status bse_create(bse_handle* out) {
     return bse_internal_set_error("cudaMallocHost failed"), BSE_ERR_NOMEM;
   }
   h->prof = prof_new();
+  BSE_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
   *out = h;
   return BSE_OK;
 }
@@ -428,6 +536,8 @@ bse_status bse_destroy(bse_handle h) {
   if (h->ws) cudaFree(h->ws);
   if (h->io) cudaFree(h->io);
   if (h->host_status) cudaFreeHost(h->host_status);
+  if (h->bws) cudaFree(h->bws);
+  if (h->bdesc_host) cudaFreeHost(h->bdesc_host);
   delete h;
   return BSE_OK;
 }

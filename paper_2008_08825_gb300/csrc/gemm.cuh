@@ -41,7 +41,7 @@ struct GemmParams {
 };
 
 template <typename T>
-GemmParams<T> gemm_params(int64_t m, int64_t n, int64_t k, int opA, const T* A, int64_t lda, int opB,
+__host__ __device__ inline GemmParams<T> gemm_params(int64_t m, int64_t n, int64_t k, int opA, const T* A, int64_t lda, int opB,
                           const T* B, int64_t ldb, T alpha, T beta, T* C, int64_t ldc) {
   GemmParams<T> p;
   p.m = m, p.n = n, p.k = k;

@@ -106,3 +106,11 @@ bse_status gebrd_backtransform(cudaStream_t s, int side, int64_t n, int64_t k, c
 bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cplx* Vbuf, int64_t ldvb,
                                  int64_t c0, int64_t bs, int64_t r0, const cplx* tau, cplx* Vout,
                                  int64_t ldv, cplx* tmp, const int64_t* status);
+
+// ---- batched.cu ----  persistent one-CTA-per-instance Cholesky-method solver
+size_t batched_inst_bytes(int64_t n, int64_t k);
+int batched_max_n();
+size_t batched_desc_bytes();
+void batched_fill_desc(void* slot, int64_t n, int64_t k, const void* A, const void* B, double* omega, void* X,
+                       void* Y, char* ws, int64_t* status);
+bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid);

@@ -205,7 +205,7 @@ def test_kappa_sweep_vs_oracle(kappa, method, dev):
 
 def test_batched_sizes_lowest_32(dev):
     """A sample of the 512-instance workload (n log-uniform in [32, 1024]),
-    lowest 32 pairs of each, against the oracle."""
+    lowest 32 pairs of each, against the oracle: subset solves of both methods."""
     sizes = inputs.batched_sizes()
     for i in [0, 1, 2, 3, 5, 8, 13, 21]:
         n = int(sizes[i])
@@ -216,6 +216,74 @@ def test_batched_sizes_lowest_32(dev):
             k = len(om)
             assert np.max(np.abs(om - om_r[:k])) <= 1e-11 * om_r.max()
             _check_vectors(X, Y, X_r[:, :k], Y_r[:, :k], om_r[:k] if k > 1 else om_r[:1])
+
+
+def _batch_instances(idx, dev, sizes=None):
+    sizes = inputs.batched_sizes() if sizes is None else sizes
+    out, host = [], []
+    for i in idx:
+        A, B = inputs.base(int(sizes[i]), seed=int(i))
+        host.append((A, B))
+        out.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
+    return out, host
+
+
+def test_batched_persistent_kernel_vs_oracle(dev):
+    """One persistent launch over uneven instances (the largest sizes of the
+    512-instance workload plus small and odd ones): lowest 32 pairs of each
+    against the oracle."""
+    sizes = inputs.batched_sizes()
+    order = np.argsort(-sizes)
+    idx = list(order[:3]) + [int(np.argmin(sizes))] + [0, 1, 2, 7, 11]
+    inst, host = _batch_instances(idx, dev)
+    extra = [(np.eye(1, dtype=np.complex128) * 3.0, np.eye(1, dtype=np.complex128) * 0.5)]
+    for A, B in extra:
+        host.append((A, B))
+        inst.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
+    bt = bse.Batch(inst, k=32).run()
+    assert all(s == 0 for s in bt.status)
+    for (A, B), (om, X, Y) in zip(host, bt.results()):
+        om, X, Y = om.cpu().numpy(), X.cpu().numpy(), Y.cpu().numpy()
+        om_r, X_r, Y_r = oracle.solve_svd(A, B)
+        k = len(om)
+        assert np.max(np.abs(om - om_r[:k])) <= 1e-11 * om_r.max()
+        assert np.max(np.abs(om - om_r[:k]) / om_r[:k]) <= 1e-11
+        _check_vectors(X, Y, X_r[:, :k], Y_r[:, :k], om_r[:k] if k > 1 else om_r[:1])
+        S = X.conj().T @ X - Y.conj().T @ Y - np.eye(k)
+        assert np.linalg.norm(S) <= 1e-10
+
+
+def test_batched_full_workload_and_graph_replay(dev):
+    """All 512 instances in one launch; then the same launch captured in a CUDA
+    graph and replayed: identical bits, every status OK, spot checks against
+    the single-instance solver."""
+    sizes = inputs.batched_sizes()
+    inst, host = _batch_instances(range(len(sizes)), dev)
+    bt = bse.Batch(inst, k=32).run()
+    assert all(s == 0 for s in bt.status)
+    first = [(o.clone(), X.clone(), Y.clone()) for o, X, Y in bt.results()]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bt.enqueue(stream=s)  # warm (allocations happen outside capture)
+    s.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        bt.enqueue(stream=s)
+    for o, X, Y in bt.results():
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(bt.dstatus.abs().sum()) == 0
+    for (o1, X1, Y1), (o2, X2, Y2) in zip(first, bt.results()):
+        assert torch.equal(o1, o2) and torch.equal(X1, X2) and torch.equal(Y1, Y2)
+    for i in [5, 100, 300, 511]:
+        A, B = host[i]
+        om, X, Y = _gpu(A, B, "chol", dev, il=1, iu=min(32, A.shape[0]))
+        ob, Xb, Yb = [t.cpu().numpy() for t in bt.results()[i]]
+        assert np.max(np.abs(om - ob)) <= 1e-12 * om.max()
+        a, b = phase_align(X, Y)
+        c, d = phase_align(Xb, Yb)
+        assert max(np.abs(a - c).max(), np.abs(b - d).max()) <= 1e-9
 
 
 # --- gradient ---------------------------------------------------------------------
