@@ -81,6 +81,15 @@ bse_status bse_workspace_size(int64_t n, int method, int prec, size_t* bytes);
  * ptr = NULL to return to internally allocated workspace. */
 bse_status bse_set_workspace(bse_handle h, void* ptr, size_t bytes);
 
+/* Handle options. */
+typedef enum {
+  /* Mixed form: complex products with m*n*k below this value stay on the FP64
+   * FMA engine, larger ones use the split-operand tensor-core engine
+   * (default 1 << 24).  1 sends every product through the tensor cores. */
+  BSE_OPT_TC_MIN_MNK = 1
+} bse_option;
+bse_status bse_set_option(bse_handle h, int option, int64_t value);
+
 /*
  * Cholesky method, Alg. 2 (Section 3.2):
  *   L L^H = A - B;  M = L^H (A + B) L;  M V_M = V_M D;  Lambda = D^{1/2};
@@ -90,8 +99,15 @@ bse_status bse_set_workspace(bse_handle h, void* ptr, size_t bytes);
  * A, B     device, n x n Hermitian, lower triangle read, leading dims lda, ldb.
  * il, iu   1-based inclusive index range into the ascending omega; il = 1,
  *          iu = n returns all pairs.  k = iu - il + 1 columns are returned.
- * prec     BSE_PREC_FP64 (all arithmetic FP64).  BSE_PREC_MIXED returns
- *          BSE_ERR_NOT_IMPLEMENTED in this build.
+ * prec     BSE_PREC_FP64: all arithmetic on the FP64 pipe.
+ *          BSE_PREC_MIXED: the large complex products (Cholesky updates,
+ *          congruence, reduction updates, back-transformations, triangular
+ *          solve and products) run on the BF16 tensor cores with exact
+ *          operand splitting (8 slices of 7 bits per FP64 value, exact FP32
+ *          partial sums per level, FP64 recombination: the Ozaki scheme), so
+ *          they carry FP64-level normwise error; pivots, matrix-vector
+ *          products of the reductions, the tridiagonal solve and all
+ *          element-wise work stay FP64.
  * omega    device, k doubles, ascending.
  * X, Y     device, n x k complex, leading dims ldx, ldy; both NULL for
  *          eigenvalues only.

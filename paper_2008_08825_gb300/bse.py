@@ -81,6 +81,8 @@ def _bind(lib):
     for f in (lib.bse_solve_batched, lib.bse_solve_batched_async):
         f.argtypes = [_P, _I64, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
         f.restype = ctypes.c_int
+    lib.bse_set_option.argtypes = [_P, ctypes.c_int, _I64]
+    lib.bse_set_option.restype = ctypes.c_int
     lib.bse_profile_enable.argtypes = [_P, ctypes.c_int]
     lib.bse_profile_enable.restype = ctypes.c_int
     lib.bse_profile_read.restype = ctypes.c_int
@@ -128,12 +130,16 @@ class Handle:
     def ptr(self):
         return self._h
 
-    def reserve(self, n: int, method: str, device) -> None:
+    def reserve(self, n: int, method: str, device, precision: str = "fp64") -> None:
         need = ctypes.c_size_t(0)
-        _check(lib().bse_workspace_size(int(n), METHODS[method], 0, ctypes.byref(need)))
+        _check(lib().bse_workspace_size(int(n), METHODS[method], PRECISIONS[precision], ctypes.byref(need)))
         if self._ws is None or self._ws.numel() < need.value or self._ws.device != device:
             self._ws = torch.empty(need.value, dtype=torch.uint8, device=device)
             _check(lib().bse_set_workspace(self._h, _P(self._ws.data_ptr()), self._ws.numel()))
+
+    def set_tc_min_mnk(self, value: int) -> None:
+        """Mixed form: products with m*n*k >= value use the tensor-core engine."""
+        _check(lib().bse_set_option(self._h, 1, int(value)))
 
     def launches(self) -> int:
         return int(lib().bse_launch_count(self._h))
@@ -184,7 +190,7 @@ def solve(A: torch.Tensor, B: torch.Tensor, method: str = "chol", precision: str
     iu = n if iu is None else int(iu)
     k = max(iu - il + 1, 0)
     h = handle or default_handle()
-    h.reserve(n, method, A.device)
+    h.reserve(n, method, A.device, precision)
     Ac, Bc = _colmajor(A), _colmajor(B)
     omega = torch.empty(k, dtype=torch.float64, device=A.device)
     if vectors:

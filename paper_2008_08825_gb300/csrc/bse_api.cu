@@ -49,6 +49,7 @@ struct bse_context {
   char* bdesc_host = nullptr;  // pinned instance table
   size_t bdesc_bytes = 0;
   int sms = 0;
+  int64_t oz_min = (int64_t)1 << 24;
 };
 
 // Makes the handle's profiler current for this thread for one entry point;
@@ -65,6 +66,12 @@ struct ProfGuard {
     }
     prof_set_current(nullptr);
   }
+};
+
+// Makes the tensor-core product workspace current for one solve (mixed form).
+struct OzGuard {
+  explicit OzGuard(const OzWork& w) { oz_set_current(w); }
+  ~OzGuard() { oz_set_current(OzWork{nullptr, 0, 0}); }
 };
 
 // ---------------------------------------------------------------------------
@@ -102,6 +109,7 @@ struct TriPlan {
 };
 
 struct CholBuffers {
+  void* oz;
   int64_t* status;
   cplx *M1, *L, *Linv, *W, *P;
   HetrdWork h;
@@ -110,8 +118,9 @@ struct CholBuffers {
   cplx* tmp;
 };
 
-static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k) {
+static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k, int prec) {
   const int nbt = hetrd_panel();
+  b.oz = prec == BSE_PREC_MIXED ? pl.take<char>(oz_work_bytes(n, 8)) : nullptr;
   b.status = pl.take<int64_t>(4);
   b.M1 = pl.take<cplx>((size_t)n * n);
   b.L = pl.take<cplx>((size_t)n * n);
@@ -134,6 +143,7 @@ static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k) {
 }
 
 struct SvdBuffers {
+  void* oz;
   int64_t* status;
   cplx *L1, *L2, *Linv, *G, *Uc, *Vc, *T1;
   GebrdWork g;
@@ -142,8 +152,9 @@ struct SvdBuffers {
   cplx* tmp;
 };
 
-static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k) {
+static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k, int prec) {
   const int nbt = 32;
+  b.oz = prec == BSE_PREC_MIXED ? pl.take<char>(oz_work_bytes(n, 8)) : nullptr;
   b.status = pl.take<int64_t>(4);
   b.L1 = pl.take<cplx>((size_t)n * n);
   b.L2 = pl.take<cplx>((size_t)n * n);
@@ -173,14 +184,14 @@ static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k) {
   b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
 }
 
-static size_t plan_bytes(int64_t n, int64_t k, int method) {
+static size_t plan_bytes(int64_t n, int64_t k, int method, int prec) {
   Plan pl(nullptr);
   if (method == BSE_METHOD_CHOL) {
     CholBuffers b;
-    carve_chol(pl, b, n, k);
+    carve_chol(pl, b, n, k, prec);
   } else {
     SvdBuffers b;
-    carve_svd(pl, b, n, k);
+    carve_svd(pl, b, n, k, prec);
   }
   return pl.off + 256;
 }
@@ -243,8 +254,7 @@ static bse_status check_common(bse_handle h, int64_t n, const double* A, int64_t
   if (il < 1 || iu > n || il > iu) return bse_internal_set_error("need 1 <= il <= iu <= n"), BSE_ERR_ARG;
   if ((X == nullptr) != (Y == nullptr)) return bse_internal_set_error("X and Y must both be given or both NULL"), BSE_ERR_ARG;
   if (X && (ldx < n || ldy < n)) return bse_internal_set_error("ldx or ldy < n"), BSE_ERR_ARG;
-  if (prec == BSE_PREC_MIXED) return bse_internal_set_error("mixed precision is not available in this build"), BSE_ERR_NOT_IMPLEMENTED;
-  if (prec != BSE_PREC_FP64) return bse_internal_set_error("unknown precision"), BSE_ERR_ARG;
+  if (prec != BSE_PREC_FP64 && prec != BSE_PREC_MIXED) return bse_internal_set_error("unknown precision"), BSE_ERR_ARG;
   return BSE_OK;
 }
 
@@ -266,14 +276,15 @@ static bse_status finish(bse_context* h, cudaStream_t s, const int64_t* dstatus,
 }
 
 static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64_t lda, const cplx* B, int64_t ldb,
-                                 int64_t il, int64_t iu, double* omega, cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
-                                 bse_info* info, cudaStream_t s) {
+                                 int64_t il, int64_t iu, int prec, double* omega, cplx* X, int64_t ldx, cplx* Y,
+                                 int64_t ldy, bse_info* info, cudaStream_t s) {
   const int64_t k = iu - il + 1;
   void* ws;
-  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_CHOL), &ws));
+  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_CHOL, prec), &ws));
   Plan pl(ws);
   CholBuffers b;
-  carve_chol(pl, b, n, k);
+  carve_chol(pl, b, n, k, prec);
+  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min});
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
@@ -337,14 +348,15 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
 }
 
 static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_t lda, const cplx* B, int64_t ldb,
-                                int64_t il, int64_t iu, double* omega, cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
-                                bse_info* info, cudaStream_t s) {
+                                int64_t il, int64_t iu, int prec, double* omega, cplx* X, int64_t ldx, cplx* Y,
+                                int64_t ldy, bse_info* info, cudaStream_t s) {
   const int64_t k = iu - il + 1;
   void* ws;
-  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_SVD), &ws));
+  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_SVD, prec), &ws));
   Plan pl(ws);
   SvdBuffers b;
-  carve_svd(pl, b, n, k);
+  carve_svd(pl, b, n, k, prec);
+  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min});
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
@@ -547,7 +559,7 @@ const char* bse_last_error(void) { return g_err.c_str(); }
 bse_status bse_workspace_size(int64_t n, int method, int prec, size_t* bytes) {
   if (!bytes || n < 0 || (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) || (prec != BSE_PREC_FP64 && prec != BSE_PREC_MIXED))
     return bse_internal_set_error("bad argument to bse_workspace_size"), BSE_ERR_ARG;
-  *bytes = plan_bytes(n, n > 0 ? n : 1, method);
+  *bytes = plan_bytes(n, n > 0 ? n : 1, method, prec);
   return BSE_OK;
 }
 
@@ -564,8 +576,8 @@ bse_status bse_solve_chol(bse_handle h, int64_t n, const double* A, int64_t lda,
                           int64_t ldy, bse_info* info, void* stream) {
   bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
   if (r != BSE_OK || n == 0) return r;
-  return solve_chol_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, omega, (cplx*)X, ldx, (cplx*)Y, ldy,
-                        info, (cudaStream_t)stream);
+  return solve_chol_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, prec, omega, (cplx*)X, ldx, (cplx*)Y,
+                        ldy, info, (cudaStream_t)stream);
 }
 
 bse_status bse_solve_svd(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
@@ -573,8 +585,8 @@ bse_status bse_solve_svd(bse_handle h, int64_t n, const double* A, int64_t lda, 
                          int64_t ldy, bse_info* info, void* stream) {
   bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
   if (r != BSE_OK || n == 0) return r;
-  return solve_svd_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, omega, (cplx*)X, ldx, (cplx*)Y, ldy,
-                       info, (cudaStream_t)stream);
+  return solve_svd_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, prec, omega, (cplx*)X, ldx, (cplx*)Y,
+                       ldy, info, (cudaStream_t)stream);
 }
 
 bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t ldx, const double* Y, int64_t ldy,
@@ -623,8 +635,8 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
   if (X) dX = pl.take<cplx>((size_t)n * k), dY = pl.take<cplx>((size_t)n * k);
   BSE_CUDA(cudaMemcpy2DAsync(dA, sizeof(cplx) * n, A, sizeof(cplx) * lda, sizeof(cplx) * n, n, cudaMemcpyHostToDevice, s));
   BSE_CUDA(cudaMemcpy2DAsync(dB, sizeof(cplx) * n, B, sizeof(cplx) * ldb, sizeof(cplx) * n, n, cudaMemcpyHostToDevice, s));
-  r = method == BSE_METHOD_CHOL ? solve_chol_dev(h, n, dA, n, dB, n, il, iu, dom, dX, n, dY, n, info, s)
-                                : solve_svd_dev(h, n, dA, n, dB, n, il, iu, dom, dX, n, dY, n, info, s);
+  r = method == BSE_METHOD_CHOL ? solve_chol_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s)
+                                : solve_svd_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s);
   if (r != BSE_OK) return r;
   BSE_CUDA(cudaMemcpyAsync(omega, dom, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   if (X) {
@@ -638,6 +650,16 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
 int64_t bse_launch_count(bse_handle h) {
   (void)h;
   return (int64_t)bse_total_launches();
+}
+
+bse_status bse_set_option(bse_handle h, int option, int64_t value) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  if (option == BSE_OPT_TC_MIN_MNK) {
+    if (value < 1) return bse_internal_set_error("BSE_OPT_TC_MIN_MNK must be >= 1"), BSE_ERR_ARG;
+    h->oz_min = value;
+    return BSE_OK;
+  }
+  return bse_internal_set_error("unknown option"), BSE_ERR_ARG;
 }
 
 bse_status bse_profile_enable(bse_handle h, int enable) {

@@ -10,6 +10,7 @@
 #include <atomic>
 
 #include "gemm_tile.cuh"
+#include "kernels.cuh"
 #include "prof.cuh"
 
 static std::atomic<long long> g_launches{0};
@@ -84,6 +85,16 @@ static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
   return BSE_OK;
 }
 
-bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) { return gemm_launch<cplx, 8>(s, p); }
+bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
+  const OzWork oz = oz_current();
+  if (oz.ptr && p.opA != OPT && p.opB != OPT && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
+    const bool prof = prof_current() != nullptr;
+    if (prof) prof_gemm_begin(s);
+    const bse_status r = gemm_z_oz_raw(s, p);
+    if (prof) prof_gemm_end(s, useful_macs(p) * 8.0);
+    return r;
+  }
+  return gemm_launch<cplx, 8>(s, p);
+}
 bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) { return gemm_launch<double, 16>(s, p); }
 bse_status gemm_f(cudaStream_t s, const GemmParams<float>& p) { return gemm_launch<float, 32>(s, p); }

@@ -114,3 +114,14 @@ size_t batched_desc_bytes();
 void batched_fill_desc(void* slot, int64_t n, int64_t k, const void* A, const void* B, double* omega, void* X,
                        void* Y, char* ws, int64_t* status);
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid);
+
+// ---- ozgemm.cu ----  FP64-accurate complex GEMM on the BF16 tensor cores
+struct OzWork {
+  void* ptr;      // slice / scale workspace (NULL: tensor-core products off)
+  size_t bytes;
+  int64_t min_mnk;  // products with m*n*k below this stay on the DFMA engine
+};
+void oz_set_current(const OzWork& w);
+OzWork oz_current();
+size_t oz_work_bytes(int64_t maxdim, int slices);
+bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p);

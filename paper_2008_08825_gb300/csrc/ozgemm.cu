@@ -1,0 +1,422 @@
+// FP64-accurate complex GEMM on the BF16 tensor cores by exact operand
+// splitting (the Ozaki scheme): C = alpha op(A) op(B) + beta C, the same
+// contract as the DFMA engine (triangular operands, lower-only output, the
+// fused X/Y epilogue), for the large products of the solver.
+//
+// Complex operands enter as their real 2x2 embedding, interleaved so that a
+// lane's accumulator pair (c0, c1) is (Re, Im) of one complex entry:
+//   A'(i, 2kk) = Re a(i,kk),  A'(i, 2kk+1) = Im a(i,kk)
+//   B''(2kk, 2j) = Re b,  B''(2kk+1, 2j) = -Im b,  B''(2kk, 2j+1) = Im b,  B''(2kk+1, 2j+1) = Re b
+// so Re c(i,j) = C'(i, 2j) and Im c(i,j) = C'(i, 2j+1) with C' = A' B''.
+//
+// Splitting (per row of A', per column pair of B''): with 2^e the smallest
+// power of two above the row's (column's) largest |Re|, |Im|, every entry
+// v = 2^e sum_{t=1..S} 2^{-7t} q_t with integers |q_1| <= 128, |q_t| <= 64
+// (round to nearest at each step, exact in FP64).  Slice t is stored as the
+// BF16 number q_t 2^{-7(t-1)} -- exact (<= 8 significant bits).  The product
+// keeps the pairs t + u <= S + 1; a pair's BF16 products at level l = t + u
+// carry the common factor 2^{-7(l-2)}, so the FP32 tensor-core accumulation
+// of one level is exact while its integer partial sum stays below 2^24
+// (guaranteed for 512 consecutive k' at every level).  Levels 2..6 therefore
+// accumulate separately and exactly and are added into FP64 accumulators
+// every 512 k'; levels >= 7 share one FP32 accumulator (their rounding is
+// below 2^-53 of the result).  The dropped pairs (t + u > S + 1) are below
+// 2^-7S of the row/column scale, the same order as FP64 rounding for S = 8.
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "prof.cuh"
+
+namespace {
+
+constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32;  // real rows, real cols, real k per tile
+constexpr int OZ_ROWB = 80;                          // smem bytes per tile row (64 data + 16 pad)
+constexpr int OZ_FOLD = 16;                          // k-tiles per FP64 fold (512 k')
+constexpr int OZ_NSETS = 6;                          // levels 2..6 separate, >= 7 combined
+
+__device__ __forceinline__ uint16_t bf16_bits_exact(float v) {
+  // v has <= 8 significant bits: truncation of the FP32 encoding is exact
+  return (uint16_t)(__float_as_uint(v) >> 16);
+}
+
+__device__ __forceinline__ void split_value(double v, int e, int S, float* out) {
+  double r = ldexp(v, 7 - e);  // |r| < 128
+  for (int t = 0; t < S; ++t) {
+    const double q = rint(r);
+    out[t] = (float)ldexp(q, -7 * t);
+    r = (r - q) * 128.0;
+  }
+}
+
+// ---- scales -----------------------------------------------------------------
+// ea[i] = 2048 + e_i for row i of op(A) (0 = all-zero row); fb[j] likewise for
+// column j of op(B).  Logical element (r, c) of op(X) with triangular mask.
+__device__ __forceinline__ bool op_elem(const cplx* X, int64_t ldx, int op, int tri, int64_t r, int64_t c,
+                                        int64_t R, int64_t C, cplx* out) {
+  if (r >= R || c >= C) return false;
+  if (tri == TRI_LO && c > r) return false;
+  if (tri == TRI_UP && c < r) return false;
+  cplx v = (op == OPN) ? X[r + c * ldx] : X[c + r * ldx];
+  if (op == OPC) v = cconj(v);
+  *out = v;
+  return true;
+}
+
+// rows of op(A) (m x k): one warp per row chunk; atomicMax on biased exponents
+__global__ void oz_rowexp_kernel(int64_t m, int64_t k, const cplx* A, int64_t lda, int op, int tri, int* ea) {
+  // tile of 32 rows x 32 columns, coalesced along the stored leading dimension
+  __shared__ double mx[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int q = ty; q < 32; q += 8) {
+    int64_t r, c;
+    if (op == OPN) r = r0 + tx, c = c0 + q;  // consecutive tx -> consecutive rows (stored contiguous)
+    else r = r0 + q, c = c0 + tx;
+    cplx v;
+    double a = 0.0;
+    if (op_elem(A, lda, op, tri, r, c, m, k, &v)) a = fmax(fabs(v.x), fabs(v.y));
+    if (op == OPN) mx[tx][q] = a; else mx[q][tx] = a;
+  }
+  __syncthreads();
+  if (ty == 0) {
+    double a = 0.0;
+    for (int q = 0; q < 32; ++q) a = fmax(a, mx[tx][q]);
+    if (a > 0.0 && r0 + tx < m) {
+      int e;
+      frexp(a, &e);
+      atomicMax(ea + r0 + tx, 2048 + e);
+    }
+  }
+}
+
+__global__ void oz_colexp_kernel(int64_t k, int64_t n, const cplx* B, int64_t ldb, int op, int tri, int* fb) {
+  __shared__ double mx[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;  // c: column j of op(B), r: kk
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    int64_t r, c;
+    if (op == OPN) r = r0 + tx, c = c0 + q;  // op(B) = B: rows kk contiguous
+    else r = r0 + q, c = c0 + tx;
+    cplx v;
+    double a = 0.0;
+    if (op_elem(B, ldb, op, tri, r, c, k, n, &v)) a = fmax(fabs(v.x), fabs(v.y));
+    if (op == OPN) mx[q][tx] = a; else mx[tx][q] = a;  // mx[col][row]
+  }
+  __syncthreads();
+  if (ty == 0) {
+    double a = 0.0;
+    for (int q = 0; q < 32; ++q) a = fmax(a, mx[tx][q]);
+    if (a > 0.0 && c0 + tx < n) {
+      int e;
+      frexp(a, &e);
+      atomicMax(fb + c0 + tx, 2048 + e);
+    }
+  }
+}
+
+// ---- slices -----------------------------------------------------------------
+// As: [S][Mp][Kp] bf16 (Kp = padded 2k, row-major, k' contiguous); every entry
+// of the padded extent is written (zeros outside op(A) and its triangle).
+template <int S>
+__global__ void oz_split_a_kernel(int64_t m, int64_t k, const cplx* A, int64_t lda, int op, int tri, const int* ea,
+                                  int64_t Mp, int64_t Kp, uint32_t* As) {
+  __shared__ cplx tile[32][33];  // tile[row][kk]
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    int64_t r, c;
+    if (op == OPN) r = r0 + tx, c = c0 + q;
+    else r = r0 + q, c = c0 + tx;
+    cplx v = mkc(0.0, 0.0);
+    op_elem(A, lda, op, tri, r, c, m, k, &v);
+    if (op == OPN) tile[tx][q] = v; else tile[q][tx] = v;
+  }
+  __syncthreads();
+  const int64_t Kc = Kp / 2;  // complex columns of the padded extent
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t r = r0 + q, c = c0 + tx;  // write along kk (contiguous)
+    if (r >= Mp || c >= Kc) continue;
+    const cplx v = tile[q][tx];
+    const int eb = (r < m) ? ea[r] : 0;
+    float sr[S], si[S];
+    const int e = eb ? eb - 2048 : 0;
+    split_value(v.x, e, S, sr);
+    split_value(v.y, e, S, si);
+    for (int t = 0; t < S; ++t) {
+      const uint32_t w = (uint32_t)bf16_bits_exact(sr[t]) | ((uint32_t)bf16_bits_exact(si[t]) << 16);
+      As[((int64_t)t * Mp + r) * Kc + c] = w;  // (k' = 2c, 2c+1)
+    }
+  }
+}
+
+// Bs: [S][Np][Kp] bf16 with Np = padded 2n; column j of op(B) gives rows 2j
+// (Re b, -Im b) and 2j+1 (Im b, Re b) at k' = 2kk, 2kk+1.
+template <int S>
+__global__ void oz_split_b_kernel(int64_t k, int64_t n, const cplx* B, int64_t ldb, int op, int tri, const int* fb,
+                                  int64_t Np, int64_t Kp, uint32_t* Bs) {
+  __shared__ cplx tile[32][33];  // tile[j][kk]
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;  // j, kk
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    int64_t r, c;
+    if (op == OPN) r = r0 + tx, c = c0 + q;
+    else r = r0 + q, c = c0 + tx;
+    cplx v = mkc(0.0, 0.0);
+    op_elem(B, ldb, op, tri, r, c, k, n, &v);
+    if (op == OPN) tile[q][tx] = v; else tile[tx][q] = v;  // tile[j][kk]
+  }
+  __syncthreads();
+  const int64_t Kc = Kp / 2, Nc = Np / 2;
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t j = c0 + q, kk = r0 + tx;
+    if (j >= Nc || kk >= Kc) continue;
+    const cplx v = tile[q][tx];
+    const int eb = (j < n) ? fb[j] : 0;
+    float sr[S], si[S];
+    const int e = eb ? eb - 2048 : 0;
+    split_value(v.x, e, S, sr);
+    split_value(v.y, e, S, si);
+    for (int t = 0; t < S; ++t) {
+      const uint32_t w0 = (uint32_t)bf16_bits_exact(sr[t]) | ((uint32_t)bf16_bits_exact(-si[t]) << 16);
+      const uint32_t w1 = (uint32_t)bf16_bits_exact(si[t]) | ((uint32_t)bf16_bits_exact(sr[t]) << 16);
+      Bs[((int64_t)t * Np + 2 * j) * Kc + kk] = w0;
+      Bs[((int64_t)t * Np + 2 * j + 1) * Kc + kk] = w1;
+    }
+  }
+}
+
+// ---- the tensor-core product -------------------------------------------------
+struct OzArgs {
+  GemmParams<cplx> p;
+  const uint32_t* As;
+  const uint32_t* Bs;
+  const int* ea;
+  const int* fb;
+  int64_t Mp, Np, Kp;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int S>
+__global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
+  extern __shared__ __align__(128) unsigned char osm[];
+  const GemmParams<cplx>& p = z.p;
+  const int64_t i0 = (int64_t)blockIdx.y * OZ_BM;        // real rows = complex rows
+  const int64_t jr0 = (int64_t)blockIdx.x * OZ_BN;       // real columns
+  const int64_t jc0 = jr0 / 2;                           // complex columns
+  if (i0 >= p.m || jc0 >= p.n) return;
+  if (p.lowerC && jc0 > i0 + OZ_BM - 1) return;
+  if (p.status && *(volatile const int64_t*)p.status) return;
+  // k-range from the triangular structure (complex), then real k' tiles
+  int64_t kb = 0, ke = p.k;
+  if (p.triA == TRI_LO) ke = min(ke, i0 + OZ_BM);
+  if (p.triA == TRI_UP) kb = max(kb, i0);
+  if (p.triB == TRI_LO) kb = max(kb, jc0);
+  if (p.triB == TRI_UP) ke = min(ke, jc0 + OZ_BN / 2);
+  int64_t kb2 = (2 * kb / OZ_BK) * OZ_BK, ke2 = 2 * ke;
+  const int64_t ntile = ke2 > kb2 ? (ke2 - kb2 + OZ_BK - 1) / OZ_BK : 0;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, warp tile 32 x 16
+  const int g = lane >> 2, tg = lane & 3;
+
+  constexpr int SLICE_BYTES = OZ_BM * OZ_ROWB;           // 64 rows x 80 B
+  constexpr int STAGE_BYTES = 2 * S * SLICE_BYTES;       // A and B
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(osm);
+  const int64_t Kc = z.Kp / 2;  // 32-bit words per slice row
+
+  auto issue = [&](int64_t kt, int stage) {
+    const int64_t kw = (kb2 + kt * OZ_BK) / 2;  // word offset of the tile in a row
+    const uint32_t st = sbase + stage * STAGE_BYTES;
+    // A: S slices x 64 rows x 4 chunks; B: S x 64 x 4
+    for (int c = tid; c < 2 * S * 256; c += 256) {
+      const int which = c / (S * 256);
+      const int rem = c % (S * 256);
+      const int t = rem / 256, row = (rem % 256) / 4, ch = rem % 4;
+      const uint32_t* src;
+      if (which == 0) src = z.As + ((int64_t)t * z.Mp + i0 + row) * Kc + kw + ch * 4;
+      else src = z.Bs + ((int64_t)t * z.Np + jr0 + row) * Kc + kw + ch * 4;
+      const uint32_t dst = st + (which * S + t) * SLICE_BYTES + row * OZ_ROWB + ch * 16;
+      cp_async16(dst, src);
+    }
+  };
+
+  double acc64[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc64[q] = 0.0;
+  float acc[OZ_NSETS][16];
+#pragma unroll
+  for (int s = 0; s < OZ_NSETS; ++s)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[s][q] = 0.f;
+
+  if (ntile > 0) {
+    issue(0, 0);
+    cp_commit();
+  }
+  for (int64_t kt = 0; kt < ntile; ++kt) {
+    const int stage = (int)(kt & 1);
+    if (kt + 1 < ntile) issue(kt + 1, stage ^ 1);
+    cp_commit();
+    cp_wait1();
+    __syncthreads();
+    const uint32_t st = sbase + stage * STAGE_BYTES;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        uint32_t a[2][4];
+        const uint32_t abase = st + t * SLICE_BYTES;
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+          const int row = wm * 32 + mi * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+          const int col = ks * 16 + (lane >> 4) * 8;  // bf16 index
+          ldsm_x4(abase + row * OZ_ROWB + col * 2, a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+        }
+#pragma unroll
+        for (int u = 0; u < S - t; ++u) {  // u index 0-based: level (t+1)+(u+1) = t + u + 2 <= S + 1
+          const uint32_t bbase = st + (S + u) * SLICE_BYTES;
+          const int nrow = wn * 16 + (lane & 7) + (lane >> 4) * 8;
+          const int kcol = ks * 16 + ((lane >> 3) & 1) * 8;
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4(bbase + nrow * OZ_ROWB + kcol * 2, b0, b1, b2, b3);
+          constexpr int dummy = 0;
+          (void)dummy;
+          const int lev = t + u;  // 0-based level (l - 2)
+          const int set = lev < OZ_NSETS - 1 ? lev : OZ_NSETS - 1;
+#pragma unroll
+          for (int mi = 0; mi < 2; ++mi) {
+            mma_bf16(&acc[set][(mi * 2 + 0) * 4], a[mi], b0, b1);
+            mma_bf16(&acc[set][(mi * 2 + 1) * 4], a[mi], b2, b3);
+          }
+        }
+      }
+    }
+    if ((kt + 1) % OZ_FOLD == 0 || kt + 1 == ntile) {
+#pragma unroll
+      for (int s = 0; s < OZ_NSETS; ++s)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          acc64[q] += (double)acc[s][q];
+          acc[s][q] = 0.f;
+        }
+    }
+    __syncthreads();
+  }
+  cp_wait0();
+
+  // epilogue: (c0, c1) / (c2, c3) of tile (mi, ni) are Re/Im of one entry
+  const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t i = i0 + wm * 32 + mi * 16 + g + 8 * h;
+        const int64_t j = jc0 + wn * 8 + ni * 4 + tg;
+        if (i >= p.m || j >= p.n) continue;
+        if (p.lowerC && i < j) continue;
+        const int q = (mi * 2 + ni) * 4 + 2 * h;
+        const int ei = z.ea[i], fj = z.fb[j];
+        double re = 0.0, im = 0.0;
+        if (ei && fj) {
+          const int sc = (ei - 2048) + (fj - 2048) - 14;
+          re = ldexp(acc64[q], sc);
+          im = ldexp(acc64[q + 1], sc);
+        }
+        cplx v = cmul(p.alpha, mkc(re, im));
+        if (p.epi == EPI_XY) {
+          const cplx v1 = p.P[i + j * p.ldp];
+          const double s1 = p.c1[j], s2 = p.c2[j];
+          const cplx x1 = cscale(v1, 0.5 * s1), x2 = cscale(v, 0.5 * s2);
+          p.C[i + j * p.ldc] = cadd(x1, x2);
+          p.Y[i + j * p.ldy] = csub(x2, x1);
+        } else {
+          if (use_beta) v = cadd(v, cmul(p.beta, p.C[i + j * p.ldc]));
+          p.C[i + j * p.ldc] = v;
+        }
+      }
+}
+
+}  // namespace
+
+// Workspace (thread-current, set by the solve entry points)
+static thread_local OzWork g_oz = {nullptr, 0, 0};
+void oz_set_current(const OzWork& w) { g_oz = w; }
+OzWork oz_current() { return g_oz; }
+
+size_t oz_work_bytes(int64_t maxdim, int slices) {
+  const int64_t Mp = (maxdim + OZ_BM - 1) / OZ_BM * OZ_BM;
+  const int64_t Np = (2 * maxdim + OZ_BN - 1) / OZ_BN * OZ_BN;
+  const int64_t Kp = (2 * maxdim + OZ_BK - 1) / OZ_BK * OZ_BK;
+  return (size_t)slices * 2 * (size_t)Kp * (size_t)(Mp + Np) + (size_t)(Mp + Np) * 4 + 1024;
+}
+
+template <int S>
+static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p) {
+  const int64_t Mp = (p.m + OZ_BM - 1) / OZ_BM * OZ_BM;
+  const int64_t Np = (2 * p.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+  const int64_t Kp = (2 * p.k + OZ_BK - 1) / OZ_BK * OZ_BK;
+  const size_t need = (size_t)S * 2 * (size_t)Kp * (size_t)(Mp + Np) + (size_t)(Mp + Np) * 4 + 1024;
+  if (!g_oz.ptr || g_oz.bytes < need) {
+    bse_internal_set_error("tensor-core GEMM workspace too small");
+    return BSE_ERR_NOMEM;
+  }
+  char* base = (char*)g_oz.ptr;
+  uint32_t* As = (uint32_t*)base;
+  uint32_t* Bs = (uint32_t*)(base + (size_t)S * Mp * Kp * 2);
+  int* ea = (int*)(base + (size_t)S * (Mp + Np) * Kp * 2);
+  int* fb = ea + Mp;
+  BSE_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (Mp + Np / 2), s));
+  dim3 tb(32, 8);
+  oz_rowexp_kernel<<<dim3(ceil_div_u(p.k, 32), ceil_div_u(p.m, 32)), tb, 0, s>>>(p.m, p.k, p.A, p.lda, p.opA, p.triA, ea);
+  oz_colexp_kernel<<<dim3(ceil_div_u(p.n, 32), ceil_div_u(p.k, 32)), tb, 0, s>>>(p.k, p.n, p.B, p.ldb, p.opB, p.triB, fb);
+  oz_split_a_kernel<S><<<dim3(ceil_div_u(Kp / 2, 32), ceil_div_u(Mp, 32)), tb, 0, s>>>(p.m, p.k, p.A, p.lda, p.opA,
+                                                                                       p.triA, ea, Mp, Kp, As);
+  oz_split_b_kernel<S><<<dim3(ceil_div_u(Np / 2, 32), ceil_div_u(Kp / 2, 32)), tb, 0, s>>>(p.k, p.n, p.B, p.ldb,
+                                                                                           p.opB, p.triB, fb, Np, Kp, Bs);
+  bse_count_launch(4);
+  BSE_LAUNCH_CHECK();
+  OzArgs z;
+  z.p = p, z.As = As, z.Bs = Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np, z.Kp = Kp;
+  const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
+  static bool attr = false;
+  if (!attr) {
+    BSE_CUDA(cudaFuncSetAttribute(oz_mma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
+  oz_mma_kernel<S><<<grid, 256, smem, s>>>(z);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p) {
+  if (p.m <= 0 || p.n <= 0) return BSE_OK;
+  if (p.opA == OPT || p.opB == OPT) {
+    bse_internal_set_error("tensor-core GEMM: transpose without conjugate is not supported");
+    return BSE_ERR_ARG;
+  }
+  return oz_run<8>(s, p);
+}

@@ -391,9 +391,6 @@ def test_arguments_and_empty(dev):
     with pytest.raises(bse.BseError) as e:
         _gpu(A, B, "chol", dev, il=0, iu=2)
     assert e.value.code == 1
-    with pytest.raises(bse.BseError) as e:
-        _gpu(A, B, "svd", dev, precision="mixed")
-    assert e.value.code == 9
     z = torch.zeros((0, 0), dtype=torch.complex128, device=dev)
     om, X, Y = bse.solve(z, z)
     assert om.numel() == 0
@@ -427,3 +424,55 @@ def test_host_buffer_entry_point(dev):
         om2, X2, Y2 = bse.solve_host(A, B, method=method)
         assert np.array_equal(om, om2.numpy())
         assert np.array_equal(X, X2.numpy()) and np.array_equal(Y, Y2.numpy())
+
+
+# --- mixed form: products on the tensor cores by exact operand splitting -----------
+
+@pytest.fixture(scope="module")
+def tc_handle(dev):
+    h = bse.Handle()
+    h.set_tc_min_mnk(1)  # every complex product through the tensor-core engine
+    return h
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 33, 64, 65, 100, 129, 200, 257])
+@pytest.mark.parametrize("method", METHODS)
+def test_mixed_small_sizes_vs_oracle(n, method, dev, tc_handle):
+    A, B = _base(n, n)
+    om_r, X_r, Y_r = _oracle(n, n)
+    om, X, Y = _gpu(A, B, method, dev, precision="mixed", handle=tc_handle)
+    assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+    assert sigma_residual(X, Y) <= 1e-10
+    assert eig_residual(A, B, om, X, Y) <= 1e-14
+    _check_vectors(X, Y, X_r, Y_r, om_r)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_mixed_n2048_vs_oracle_and_fp64(method, dev):
+    n = 2048
+    A, B = _base(n, 0)
+    om_r, X_r, Y_r = _oracle(n, 0)
+    om, X, Y = _gpu(A, B, method, dev, precision="mixed")
+    om64, _, _ = _gpu(A, B, method, dev, vectors=False)
+    assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+    print(f"mixed {method}: rel.err vs oracle {np.max(np.abs(om - om_r) / om_r):.2e}, fp64 form "
+          f"{np.max(np.abs(om64 - om_r) / om_r):.2e}")
+    assert sigma_residual(X, Y) <= 1e-10
+    _check_vectors(X, Y, X_r, Y_r, om_r)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10])
+@pytest.mark.parametrize("method", METHODS)
+def test_mixed_kappa_sweep(kappa, method, dev, tc_handle):
+    n = 256
+    A, B, _ = inputs.kappa_sweep(n, kappa, seed=0)
+    om_r, _, _ = oracle.solve_svd(A, B, vectors=False)
+    om, X, Y = _gpu(A, B, method, dev, precision="mixed", handle=tc_handle)
+    if method == "svd" or kappa <= 1e6:
+        assert np.max(np.abs(om - om_r)) <= 1e-11 * om_r.max()
+    else:
+        tol = np.maximum(1e-11 * om_r.max(), 64 * np.finfo(float).eps * om_r.max() ** 2 / om_r)
+        assert np.all(np.abs(om - om_r) <= tol)
+    print(f"mixed kappa={kappa:g} {method}: rel.err(smallest)={abs(om[0] - om_r[0]) / om_r[0]:.2e}")
