@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=768)
     ap.add_argument("--methods", default="chol,svd", help="comma list of chol, svd")
+    ap.add_argument("--precisions", default="fp64,mixed", help="fp64 (headline) and/or mixed")
     ap.add_argument("--workload", default="n8192", choices=["n8192", "batched"],
                     help="n8192: the headline solve; batched: 512 uneven instances, lowest 32 pairs")
     return ap.parse_args()
@@ -238,42 +239,55 @@ def main():
     Bt = torch.from_numpy(B).to(dev)
     del A, B
     h = bse.Handle()
-    h.reserve(n, "svd", dev)
     stream = torch.cuda.current_stream()
 
     methods = [m for m in args.methods.split(",") if m]
+    precs = [q for q in args.precisions.split(",") if q]
+    kgrad = 16
+    wgrad = torch.from_numpy(inputs.grad_weights(kgrad, seed=1)).to(dev)
 
-    def step():
+    def step(prec):
+        out = []
         for m in methods:
-            bse.solve(At, Bt, method=m, handle=h)
+            om, X, Y = bse.solve(At, Bt, method=m, precision=prec, handle=h)
+            out.append(om)
+            if m == methods[0] and prec == precs[0]:
+                bse.grad(X[:, :kgrad], Y[:, :kgrad], wgrad, handle=h)  # row a9 (gradient of the lowest 16)
+        return out
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    bse.lib().bse_profile_enable(h.ptr, 1)
-    launches0 = h.launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    launches = h.launches() - launches0
-    prof = _read_profile(bse, h)
-    bse.lib().bse_profile_enable(h.ptr, 0)
-    clk = clocks.stop()
-    if pg:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed = float(t.item())
-        pg.barrier()
+    def timed(prec):
+        for _ in range(args.warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        bse.lib().bse_profile_enable(h.ptr, 1)
+        l0 = h.launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        oms = None
+        for _ in range(args.steps):
+            oms = step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        pr = _read_profile(bse, h)
+        bse.lib().bse_profile_enable(h.ptr, 0)
+        ck = clocks.stop()
+        if pg:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            el = float(t.item())
+            pg.barrier()
+        return el, h.launches() - l0, pr, ck, [o.cpu().numpy() for o in oms]
+
+    h.reserve(n, "svd", dev, "mixed" if "mixed" in precs else "fp64")
+    results = {q: timed(q) for q in precs}
+    elapsed, launches, prof, clk, om_head = results[precs[0]]
     solves = len(methods) * args.steps * world
     value = solves / elapsed
     ms_per_step = elapsed / args.steps * 1e3
@@ -293,7 +307,8 @@ def main():
             pg.barrier()
         t0 = time.perf_counter()
         for method in [bse.METHODS[m] for m in methods]:
-            code = bse.lib().bse_solve_host(h.ptr, method, n, P(Ah.data_ptr()), n, P(Bh.data_ptr()), n, 1, n, 0,
+            code = bse.lib().bse_solve_host(h.ptr, method, n, P(Ah.data_ptr()), n, P(Bh.data_ptr()), n, 1, n,
+                                            bse.PRECISIONS[precs[0]],
                                             P(om.data_ptr()), P(Xh.data_ptr()), n, P(Yh.data_ptr()), n,
                                             ctypes.byref(info), P(stream.cuda_stream))
             bse._check(code)
@@ -326,20 +341,40 @@ def main():
     if not args.no_cpu_baseline:
         cb, _ = cpu_baseline(args.cpu_sample_n, 1)
     stage_names = ["form", "cholesky", "congruence_or_product", "householder_reduction", "tridiagonal",
-                   "orthogonalisation", "back_transformation", "post_processing", "gradient", "other"]
+                   "orthogonalisation", "back_transformation", "post_processing", "gradient", "refinement"]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"BSE form-I n={n} complex128, base generator (seed = rank), one CHOL (Alg. 2) "
                                f"and one SVD (Alg. 3) solve per step, all n eigenpairs with vectors, FP64",
-                   "n": n, "methods": methods, "precision": "fp64", "parallelism": "replicas",
+                   "n": n, "methods": methods, "precision": precs[0], "gradient_k": kgrad,
+                   "parallelism": "replicas",
                    "l2": "inputs (2 x 1.07 GB) larger than L2, no flush"},
         "model_tflops": model * args.steps * world / elapsed / 1e12,
         "model_flops_per_step": model,
         "stage_ms_per_step": {k: v / args.steps for k, v in zip(stage_names, prof["stage_ms"]) if v > 0},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cb,
     }
+    if "mixed" in results and precs[0] != "mixed":
+        el_m, l_m, pr_m, ck_m, om_m = results["mixed"]
+        diff = max(float(np.max(np.abs(a - b) / b)) for a, b in zip(om_m, om_head))
+        mma_flops = pr_m["gemm_flops"] * 36.0  # 36 BF16 slice products per FP64-equivalent product
+        line["mixed"] = {
+            "value": len(methods) * args.steps * world / el_m, "unit": "solves/s", "ms_per_step": el_m / args.steps * 1e3,
+            "speedup_vs_fp64": elapsed / el_m, "model_tflops": model * args.steps * world / el_m / 1e12,
+            "max_rel_diff_omega_vs_fp64": diff, "gpu_launches": l_m, "clocks": ck_m,
+            "stage_ms_per_step": {k: v / args.steps for k, v in zip(stage_names, pr_m["stage_ms"]) if v > 0},
+            "roofline": {"bound": "tensor", "kernel": "oz_mma_kernel<8> (BF16 mma.sync, split FP64 operands)",
+                         "achieved": mma_flops / (pr_m["gemm_ms"] / 1e3) / 1e12 if pr_m["gemm_ms"] > 0 else None,
+                         "peak": 1928.9, "unit": "TFLOP/s",
+                         "frac": (mma_flops / (pr_m["gemm_ms"] / 1e3) / 1e12 / 1928.9) if pr_m["gemm_ms"] > 0 else None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS tcgen05); the legacy mma.sync "
+                                        "path measured 601.7 TFLOP/s on this part (profiles/fp64_peaks_gb300.md)",
+                         "fp64_equivalent_tflops": pr_m["gemm_flops"] / (pr_m["gemm_ms"] / 1e3) / 1e12
+                         if pr_m["gemm_ms"] > 0 else None,
+                         "traffic": None},
+        }
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -56,8 +56,9 @@ typedef enum { BSE_METHOD_CHOL = 0, BSE_METHOD_SVD = 1 } bse_method;
 
 typedef struct bse_info {
   int64_t info;          /* failing column (1-based) for NOT_PD, else 0 */
-  double err_est;        /* mixed form: estimated relative eigenvalue error after refinement */
-  int32_t refine_iters;  /* mixed form: refinement sweeps used */
+  double err_est;        /* mixed form with vectors: max_i ||Hcal1 v_i - omega_i Sigma v_i|| /
+                            (omega_i ||v_i||) after refinement, else 0 */
+  int32_t refine_iters;  /* mixed form with vectors: 1 (one Rayleigh-quotient sweep), else 0 */
   int32_t reserved;
 } bse_info;
 
@@ -107,7 +108,11 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value);
  *          partial sums per level, FP64 recombination: the Ozaki scheme), so
  *          they carry FP64-level normwise error; pivots, matrix-vector
  *          products of the reductions, the tridiagonal solve and all
- *          element-wise work stay FP64.
+ *          element-wise work stay FP64.  With vectors, omega is then
+ *          refined against the original A, B: omega_i becomes the Rayleigh
+ *          quotient v_i^H Hcal1 v_i / v_i^H Sigma v_i of the pencil
+ *          (Hcal1, Sigma) of Eq. (1) (second order in the vector error), and
+ *          info->err_est reports the largest relative residual.
  * omega    device, k doubles, ascending.
  * X, Y     device, n x k complex, leading dims ldx, ldy; both NULL for
  *          eigenvalues only.
@@ -210,7 +215,8 @@ int64_t bse_launch_count(bse_handle h);
 #define BSE_NSTAGES 10
 /* stage index: 0 form A+-B, 1 Cholesky, 2 congruence / product L1^H L2,
  * 3 Householder reduction, 4 tridiagonal eigensolve, 5 orthogonalisation,
- * 6 back-transformation, 7 post-processing + final setup, 8 gradient, 9 other */
+ * 6 back-transformation, 7 post-processing + final setup, 8 gradient,
+ * 9 refinement (mixed form) */
 typedef struct bse_profile_data {
   double stage_ms[BSE_NSTAGES];
   int64_t stage_calls[BSE_NSTAGES];

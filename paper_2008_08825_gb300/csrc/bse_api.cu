@@ -108,8 +108,23 @@ struct TriPlan {
   }
 };
 
+struct RefineBufs {
+  cplx *F1, *F2, *work;  // full M1, full M2, 4 n k
+  double *est, *est_max;
+};
+
+static void carve_refine(Plan& pl, RefineBufs& r, int64_t n, int64_t k, int prec) {
+  const bool on = prec == BSE_PREC_MIXED;
+  r.F1 = on ? pl.take<cplx>((size_t)n * n) : nullptr;
+  r.F2 = on ? pl.take<cplx>((size_t)n * n) : nullptr;
+  r.work = on ? pl.take<cplx>((size_t)4 * n * k) : nullptr;
+  r.est = on ? pl.take<double>(k) : nullptr;
+  r.est_max = on ? pl.take<double>(1) : nullptr;
+}
+
 struct CholBuffers {
   void* oz;
+  RefineBufs rf;
   int64_t* status;
   cplx *M1, *L, *Linv, *W, *P;
   HetrdWork h;
@@ -121,6 +136,7 @@ struct CholBuffers {
 static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k, int prec) {
   const int nbt = hetrd_panel();
   b.oz = prec == BSE_PREC_MIXED ? pl.take<char>(oz_work_bytes(n, 8)) : nullptr;
+  carve_refine(pl, b.rf, n, k, prec);
   b.status = pl.take<int64_t>(4);
   b.M1 = pl.take<cplx>((size_t)n * n);
   b.L = pl.take<cplx>((size_t)n * n);
@@ -144,6 +160,7 @@ static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k, int prec)
 
 struct SvdBuffers {
   void* oz;
+  RefineBufs rf;
   int64_t* status;
   cplx *L1, *L2, *Linv, *G, *Uc, *Vc, *T1;
   GebrdWork g;
@@ -155,6 +172,7 @@ struct SvdBuffers {
 static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k, int prec) {
   const int nbt = 32;
   b.oz = prec == BSE_PREC_MIXED ? pl.take<char>(oz_work_bytes(n, 8)) : nullptr;
+  carve_refine(pl, b.rf, n, k, prec);
   b.status = pl.take<int64_t>(4);
   b.L1 = pl.take<cplx>((size_t)n * n);
   b.L2 = pl.take<cplx>((size_t)n * n);
@@ -258,14 +276,18 @@ static bse_status check_common(bse_handle h, int64_t n, const double* A, int64_t
   return BSE_OK;
 }
 
-static bse_status finish(bse_context* h, cudaStream_t s, const int64_t* dstatus, bse_info* info) {
+static bse_status finish(bse_context* h, cudaStream_t s, const int64_t* dstatus, bse_info* info,
+                         const double* est_max = nullptr) {
   BSE_CUDA(cudaMemcpyAsync(h->host_status, dstatus, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (est_max) BSE_CUDA(cudaMemcpyAsync(h->host_status + 2, est_max, sizeof(double), cudaMemcpyDeviceToHost, s));
   BSE_CUDA(cudaStreamSynchronize(s));
   const int64_t code = h->host_status[0];
   if (info) {
     info->info = h->host_status[1];
-    info->err_est = 0.0;
-    info->refine_iters = 0;
+    double e = 0.0;
+    if (est_max) memcpy(&e, h->host_status + 2, sizeof(double));
+    info->err_est = e;
+    info->refine_iters = est_max ? 1 : 0;
   }
   if (code != 0) {
     char buf[128];
@@ -294,6 +316,10 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
     StageScope sc(0, s);
     TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.M1, n, 1));
     TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L, n, 0));
+    if (b.rf.F1 && X) {
+      TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.rf.F1, n, 1));
+      TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.rf.F2, n, 1));
+    }
   }
   {
     StageScope sc(1, s);
@@ -344,6 +370,11 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
   p3.epi = EPI_XY;
   p3.P = b.P, p3.ldp = n, p3.c1 = b.c1, p3.c2 = b.c2, p3.Y = Y, p3.ldy = ldy;
   TRY(gemm_z(s, p3));
+  if (b.rf.F1) {
+    StageScope scr(9, s);
+    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st));
+    return finish(h, s, st, info, b.rf.est_max);
+  }
   return finish(h, s, st, info);
 }
 
@@ -365,6 +396,10 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
     StageScope sc(0, s);
     TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.L1, n, 0));
     TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.L2, n, 0));
+    if (b.rf.F1 && X) {
+      TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.rf.F1, n, 1));
+      TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.rf.F2, n, 1));
+    }
   }
   {
     StageScope sc(1, s);
@@ -420,6 +455,11 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
   p2.epi = EPI_XY;
   p2.P = b.T1, p2.ldp = n, p2.c1 = b.c1, p2.c2 = b.c2, p2.Y = Y, p2.ldy = ldy;
   TRY(gemm_z(s, p2));
+  if (b.rf.F1) {
+    StageScope scr(9, s);
+    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st));
+    return finish(h, s, st, info, b.rf.est_max);
+  }
   return finish(h, s, st, info);
 }
 
@@ -531,7 +571,7 @@ bse_status bse_create(bse_handle* out) {
   if (!out) return bse_internal_set_error("NULL output"), BSE_ERR_ARG;
   bse_context* h = new bse_context();
   BSE_CUDA(cudaGetDevice(&h->device));
-  if (cudaMallocHost(&h->host_status, 4 * sizeof(int64_t)) != cudaSuccess) {
+  if (cudaMallocHost(&h->host_status, 4 * sizeof(int64_t)) != cudaSuccess) {  // code, info, err_est
     cudaGetLastError();
     delete h;
     return bse_internal_set_error("cudaMallocHost failed"), BSE_ERR_NOMEM;

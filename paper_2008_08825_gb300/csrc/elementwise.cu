@@ -244,3 +244,103 @@ bse_status grad_outer(cudaStream_t s, int64_t n, int64_t k, const cplx* X, int64
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Refinement of omega against the original A, B (mixed form).  With
+// V1 = X - Y, V2 = X + Y and A = (M1 + M2)/2, B = (M1 - M2)/2:
+//   v^H Hcal1 v = (v2^H M1 v2 + v1^H M2 v1)/2,   v^H Sigma v = Re(v1^H v2),
+//   Hcal1 v - omega Sigma v = [ (M1 v2 + M2 v1)/2 - omega x ; (M1 v2 - M2 v1)/2 + omega y ].
+// omega_i is replaced by the Rayleigh quotient of the pencil (Hcal1, Sigma)
+// (second-order accurate in the eigenvector error) and est_i = ||r_i|| /
+// (omega_i ||v_i||) is the relative residual.
+__global__ void sum_diff_kernel(int64_t n, int64_t k, const cplx* X, int64_t ldx, const cplx* Y, int64_t ldy,
+                                cplx* V1, cplx* V2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n || j >= k) return;
+  const cplx x = X[IDX2(i, j, ldx)], y = Y[IDX2(i, j, ldy)];
+  V1[IDX2(i, j, n)] = csub(x, y);
+  V2[IDX2(i, j, n)] = cadd(x, y);
+}
+
+__global__ void __launch_bounds__(256) refine_omega_kernel(int64_t n, const cplx* X, int64_t ldx, const cplx* Y,
+                                                           int64_t ldy, const cplx* V1, const cplx* V2,
+                                                           const cplx* P1, const cplx* P2, double* omega,
+                                                           double* est, const int64_t* status) {
+  __shared__ double red[8][8];
+  if (*(volatile const int64_t*)status) return;
+  const int64_t j = blockIdx.x;
+  const double om = omega[j];
+  double s[6] = {0, 0, 0, 0, 0, 0};  // Re a, Re b, Re(v1^H v2), ||r||^2, ||v||^2, unused
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const cplx v1 = V1[IDX2(i, j, n)], v2 = V2[IDX2(i, j, n)];
+    const cplx p1 = P1[IDX2(i, j, n)], p2 = P2[IDX2(i, j, n)];
+    const cplx x = X[IDX2(i, j, ldx)], y = Y[IDX2(i, j, ldy)];
+    s[0] += v2.x * p1.x + v2.y * p1.y;
+    s[1] += v1.x * p2.x + v1.y * p2.y;
+    s[2] += v1.x * v2.x + v1.y * v2.y;
+    const cplx top = csub(cscale(cadd(p1, p2), 0.5), cscale(x, om));
+    const cplx bot = cadd(cscale(csub(p1, p2), 0.5), cscale(y, om));
+    s[3] += cabs2(top) + cabs2(bot);
+    s[4] += cabs2(x) + cabs2(y);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int q = 0; q < 5; ++q) {
+    double v = s[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[q][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[5];
+    for (int q = 0; q < 5; ++q) {
+      t[q] = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t[q] += red[q][ww];
+    }
+    est[j] = sqrt(t[3]) / (om * sqrt(t[4]));
+    omega[j] = 0.5 * (t[0] + t[1]) / t[2];
+  }
+}
+
+__global__ void max_kernel(int64_t k, const double* v, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) m = fmax(m, v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+    *out = r;
+  }
+}
+
+bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, const cplx* M2, const cplx* X,
+                        int64_t ldx, const cplx* Y, int64_t ldy, cplx* work, double* omega, double* est,
+                        double* est_max, const int64_t* status) {
+  if (n <= 0 || k <= 0) return BSE_OK;
+  cplx* V1 = work;
+  cplx* V2 = V1 + n * k;
+  cplx* P1 = V2 + n * k;
+  cplx* P2 = P1 + n * k;
+  dim3 g(ceil_div_u(n, 256), (unsigned)k);
+  sum_diff_kernel<<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, V1, V2);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  GemmParams<cplx> a = gemm_params<cplx>(n, k, n, OPN, M1, n, OPN, V2, n, one, zero, P1, n);
+  a.status = status;
+  bse_status r = gemm_z(s, a);
+  if (r) return r;
+  GemmParams<cplx> b = gemm_params<cplx>(n, k, n, OPN, M2, n, OPN, V1, n, one, zero, P2, n);
+  b.status = status;
+  if ((r = gemm_z(s, b))) return r;
+  refine_omega_kernel<<<(unsigned)k, 256, 0, s>>>(n, X, ldx, Y, ldy, V1, V2, P1, P2, omega, est, status);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  max_kernel<<<1, 256, 0, s>>>(k, est, est_max);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}

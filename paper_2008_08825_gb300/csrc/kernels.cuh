@@ -28,6 +28,12 @@ bse_status sub_identity(cudaStream_t s, int64_t k, double* E, int64_t lde);
 // singular values, omega = lam, c1 = c2 = 1/sqrt(omega).
 bse_status finish_omega(cudaStream_t s, int64_t k, const double* lam, int mode, double* omega_out,
                         double* c1, double* c2, const int64_t* status);
+// Mixed form: Rayleigh-quotient refinement of omega against the original
+// A, B (through full Hermitian M1 = A + B, M2 = A - B) and relative residuals.
+// work: 4 n k complex.  est: k doubles, est_max: 1 double (device).
+bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, const cplx* M2, const cplx* X,
+                        int64_t ldx, const cplx* Y, int64_t ldy, cplx* work, double* omega, double* est,
+                        double* est_max, const int64_t* status);
 // zero a complex matrix block
 bse_status zero_c(cudaStream_t s, int64_t m, int64_t n, cplx* A, int64_t lda);
 // gradient (Thm. 3 item 3): dA = X W X^H + Y W Y^H, dB = X W Y^H + Y W X^H
