@@ -87,7 +87,12 @@ typedef enum {
   /* Mixed form: complex products with m*n*k below this value stay on the FP64
    * FMA engine, larger ones use the split-operand tensor-core engine
    * (default 1 << 24).  1 sends every product through the tensor cores. */
-  BSE_OPT_TC_MIN_MNK = 1
+  BSE_OPT_TC_MIN_MNK = 1,
+  /* Batched solves: resident CTAs per SM of the persistent kernel, 1 or 2
+   * (default 2).  One CTA per SM gives each instance the SM's whole FP64
+   * pipe (shorter critical path for the largest instances); two hide more
+   * latency.  Chosen per workload by the autotuner (autotune.py). */
+  BSE_OPT_BATCH_CTAS_PER_SM = 2
 } bse_option;
 bse_status bse_set_option(bse_handle h, int option, int64_t value);
 

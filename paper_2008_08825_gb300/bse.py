@@ -141,6 +141,10 @@ class Handle:
         """Mixed form: products with m*n*k >= value use the tensor-core engine."""
         _check(lib().bse_set_option(self._h, 1, int(value)))
 
+    def set_batch_ctas_per_sm(self, value: int) -> None:
+        """Batched solves: 1 or 2 resident CTAs per SM for the persistent kernel."""
+        _check(lib().bse_set_option(self._h, 2, int(value)))
+
     def launches(self) -> int:
         return int(lib().bse_launch_count(self._h))
 

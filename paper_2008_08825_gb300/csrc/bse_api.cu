@@ -50,6 +50,7 @@ struct bse_context {
   size_t bdesc_bytes = 0;
   int sms = 0;
   int64_t oz_min = (int64_t)1 << 24;
+  int batch_cps = 2;
 };
 
 // Makes the handle's profiler current for this thread for one entry point;
@@ -526,7 +527,7 @@ static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* 
   }
   BSE_CUDA(cudaMemcpyAsync(ddesc, h->bdesc_host, batched_desc_bytes() * count, cudaMemcpyHostToDevice, s));
   BSE_CUDA(cudaMemsetAsync(dstat, 0, 16 * count, s));
-  const int grid = (int)std::min<int64_t>(count, (int64_t)h->sms * 2);
+  const int grid = (int)std::min<int64_t>(count, (int64_t)h->sms * h->batch_cps);
   TRY(batched_chol_launch(s, ddesc, count, counter, grid));
   if (dstatus_out) *dstatus_out = dstat;
   return BSE_OK;
@@ -697,6 +698,11 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value) {
   if (option == BSE_OPT_TC_MIN_MNK) {
     if (value < 1) return bse_internal_set_error("BSE_OPT_TC_MIN_MNK must be >= 1"), BSE_ERR_ARG;
     h->oz_min = value;
+    return BSE_OK;
+  }
+  if (option == BSE_OPT_BATCH_CTAS_PER_SM) {
+    if (value != 1 && value != 2) return bse_internal_set_error("BSE_OPT_BATCH_CTAS_PER_SM must be 1 or 2"), BSE_ERR_ARG;
+    h->batch_cps = (int)value;
     return BSE_OK;
   }
   return bse_internal_set_error("unknown option"), BSE_ERR_ARG;

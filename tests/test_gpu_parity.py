@@ -476,3 +476,29 @@ def test_mixed_kappa_sweep(kappa, method, dev, tc_handle):
         tol = np.maximum(1e-11 * om_r.max(), 64 * np.finfo(float).eps * om_r.max() ** 2 / om_r)
         assert np.all(np.abs(om - om_r) <= tol)
     print(f"mixed kappa={kappa:g} {method}: rel.err(smallest)={abs(om[0] - om_r[0]) / om_r[0]:.2e}")
+
+
+def test_autotuner_batched_and_threshold(dev, tmp_path, monkeypatch):
+    """The autotuner times both batched densities and the tensor-core thresholds,
+    caches its choice, and the tuned settings give the same results."""
+    from paper_2008_08825_gb300 import autotune
+
+    monkeypatch.setenv("BSE_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    sizes = inputs.batched_sizes()
+    idx = list(np.argsort(-sizes)[:4]) + list(range(12))
+    inst, _ = _batch_instances(idx, dev)
+    h = bse.Handle()
+    bt = bse.Batch(inst, k=32)
+    ref = [(o.clone(), X.clone()) for o, X, _ in bt.run(handle=h).results()]
+    r = autotune.tune_batched(bt, h)
+    assert r["ctas_per_sm"] in (1, 2) and set(r["ms"]) == {"1", "2"}
+    bt.run(handle=h)
+    for (o1, X1), (o2, X2, _) in zip(ref, bt.results()):
+        assert torch.equal(o1, o2) and torch.equal(X1, X2)  # density does not change any bit
+    A, B = _base(300, 1)
+    At, Bt = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    t = autotune.tune_tc_threshold(At, Bt, "chol", h, candidates=(1, 1 << 24))
+    assert t["tc_min_mnk"] in (1, 1 << 24)
+    import json
+    cache = json.load(open(tmp_path / "tune.json"))
+    assert len(cache) == 2
