@@ -230,8 +230,13 @@ typedef struct bse_profile_data {
   int64_t gemm_launches;
   int64_t launches;       /* all kernel launches while enabled */
 } bse_profile_data;
+/* enable: 0 off, 1 stages and GEMMs, 2 additionally every launch of the
+ * reduction and tridiagonal kernels (adds two events per launch). */
 bse_status bse_profile_enable(bse_handle h, int enable);
 bse_status bse_profile_read(bse_handle h, bse_profile_data* out);
+/* Level-2 per-kernel summary, one "name launches total_ms" line per kernel,
+ * written NUL-terminated into buf (truncated to len); returns the full length. */
+int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
 
 #ifdef __cplusplus
 }

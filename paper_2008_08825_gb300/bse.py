@@ -86,6 +86,8 @@ def _bind(lib):
     lib.bse_profile_enable.argtypes = [_P, ctypes.c_int]
     lib.bse_profile_enable.restype = ctypes.c_int
     lib.bse_profile_read.restype = ctypes.c_int
+    lib.bse_profile_kernels.argtypes = [_P, ctypes.c_char_p, ctypes.c_size_t]
+    lib.bse_profile_kernels.restype = ctypes.c_int64
     for name in ("bse_create", "bse_destroy", "bse_workspace_size", "bse_set_workspace", "bse_solve_chol",
                  "bse_solve_svd", "bse_grad", "bse_solve_host"):
         getattr(lib, name).restype = ctypes.c_int
@@ -144,6 +146,16 @@ class Handle:
     def set_batch_ctas_per_sm(self, value: int) -> None:
         """Batched solves: 1 or 2 resident CTAs per SM for the persistent kernel."""
         _check(lib().bse_set_option(self._h, 2, int(value)))
+
+    def kernel_profile(self) -> dict:
+        """Per-kernel (launches, total ms) recorded at profiling level 2."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        lib().bse_profile_kernels(self._h, buf, len(buf))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.rsplit(" ", 2)
+            out[name] = (int(cnt), float(ms))
+        return out
 
     def launches(self) -> int:
         return int(lib().bse_launch_count(self._h))

@@ -711,8 +711,14 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value) {
 bse_status bse_profile_enable(bse_handle h, int enable) {
   if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
   h->prof_on = enable ? 1 : 0;
+  prof_set_fine(h->prof, enable >= 2);
   prof_reset(h->prof);
   return BSE_OK;
+}
+
+int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len) {
+  if (!h) return -1;
+  return prof_kernel_summary(h->prof, buf, len);
 }
 
 bse_status bse_profile_read(bse_handle h, bse_profile_data* out) {

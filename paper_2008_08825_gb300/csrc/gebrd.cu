@@ -16,6 +16,7 @@
 // step (A^H u: warp per column; A v: thread per row) read the trailing
 // matrix coalesced and are bound by the FP64 pipe on GB300.
 #include "kernels.cuh"
+#include "prof.cuh"
 
 constexpr int NBB = 32;
 constexpr int BRB = 256;
@@ -276,7 +277,9 @@ __global__ void __launch_bounds__(BRB) bd_x_assemble(BdArgs a, int nch) {
 
 #define BLAUNCH(kern, grid, ...)                 \
   do {                                           \
+    prof_launch_begin(s);                        \
     kern<<<(grid), BRB, 0, s>>>(__VA_ARGS__);    \
+    prof_launch_end(s, #kern);                   \
     bse_count_launch();                          \
     BSE_LAUNCH_CHECK();                          \
   } while (0)

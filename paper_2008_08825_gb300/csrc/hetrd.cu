@@ -17,6 +17,7 @@
 // 6.8 TB/s; the part delivers 1.2), so the one-stage reduction does the same
 // FP64 work as a band reduction and saves its second back-transformation.
 #include "kernels.cuh"
+#include "prof.cuh"
 
 constexpr int NBT = 32;    // panel width
 constexpr int RB = 256;    // rows per CTA in column kernels
@@ -274,7 +275,9 @@ __global__ void tr_last_diag(int64_t n, const cplx* A, int64_t lda, double* d, c
 
 #define LAUNCH(kern, grid, blk, ...)                 \
   do {                                               \
+    prof_launch_begin(s);                            \
     kern<<<(grid), (blk), 0, s>>>(__VA_ARGS__);      \
+    prof_launch_end(s, #kern);                       \
     bse_count_launch();                              \
     BSE_LAUNCH_CHECK();                              \
   } while (0)

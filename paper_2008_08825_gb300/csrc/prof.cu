@@ -1,6 +1,9 @@
 // Event-based profiler (see prof.cuh).
+#include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <string>
 #include <vector>
 
 #include "prof.cuh"
@@ -10,11 +13,15 @@ long long bse_total_launches();
 struct Profiler {
   std::vector<cudaEvent_t> pool;
   struct Rec {
-    int kind;  // 0 stage, 1 gemm
+    int kind;  // 0 stage, 1 gemm, 2 named launch
     int stage;
     double flops;
     cudaEvent_t a, b;
+    const char* name;
   };
+  int fine = 0;
+  cudaEvent_t launch_a = nullptr;
+  std::map<std::string, std::pair<long long, double>> per_kernel;
   std::vector<Rec> open_stage[BSE_NSTAGES];
   std::vector<Rec> done;
   bse_profile_data acc;
@@ -53,6 +60,7 @@ void prof_delete(Profiler* p) {
 
 void prof_reset(Profiler* p) {
   memset(&p->acc, 0, sizeof(p->acc));
+  p->per_kernel.clear();
   p->launches0 = bse_total_launches();
 }
 
@@ -62,7 +70,7 @@ Profiler* prof_current() { return g_cur; }
 void prof_stage_begin(int stage, cudaStream_t s) {
   Profiler* p = g_cur;
   if (!p) return;
-  Profiler::Rec r{0, stage, 0.0, p->get(), nullptr};
+  Profiler::Rec r{0, stage, 0.0, p->get(), nullptr, nullptr};
   if (r.a) cudaEventRecord(r.a, s);
   p->open_stage[stage].push_back(r);
 }
@@ -87,10 +95,44 @@ void prof_gemm_begin(cudaStream_t s) {
 void prof_gemm_end(cudaStream_t s, double flops) {
   Profiler* p = g_cur;
   if (!p || !p->gemm_a) return;
-  Profiler::Rec r{1, 0, flops, p->gemm_a, p->get()};
+  Profiler::Rec r{1, 0, flops, p->gemm_a, p->get(), nullptr};
   if (r.b) cudaEventRecord(r.b, s);
   p->gemm_a = nullptr;
   p->done.push_back(r);
+}
+
+bool prof_fine() { return g_cur && g_cur->fine; }
+void prof_set_fine(Profiler* p, int fine) { p->fine = fine; }
+
+void prof_launch_begin(cudaStream_t s) {
+  Profiler* p = g_cur;
+  if (!p || !p->fine) return;
+  p->launch_a = p->get();
+  if (p->launch_a) cudaEventRecord(p->launch_a, s);
+}
+
+void prof_launch_end(cudaStream_t s, const char* name) {
+  Profiler* p = g_cur;
+  if (!p || !p->fine || !p->launch_a) return;
+  Profiler::Rec r{2, 0, 0.0, p->launch_a, p->get(), name};
+  if (r.b) cudaEventRecord(r.b, s);
+  p->launch_a = nullptr;
+  p->done.push_back(r);
+}
+
+int prof_kernel_summary(Profiler* p, char* buf, size_t len) {
+  std::string out;
+  for (auto& kv : p->per_kernel) {
+    char line[256];
+    snprintf(line, sizeof line, "%s %lld %.4f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+    out += line;
+  }
+  if (buf && len) {
+    const size_t nb = out.size() < len - 1 ? out.size() : len - 1;
+    memcpy(buf, out.data(), nb);
+    buf[nb] = 0;
+  }
+  return (int)out.size();
 }
 
 void prof_flush(Profiler* p) {
@@ -98,7 +140,11 @@ void prof_flush(Profiler* p) {
   for (auto& r : p->done) {
     float ms = 0.f;
     if (r.a && r.b && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-      if (r.kind == 0) {
+      if (r.kind == 2) {
+        auto& e = p->per_kernel[r.name];
+        e.first += 1;
+        e.second += ms;
+      } else if (r.kind == 0) {
         p->acc.stage_ms[r.stage] += ms;
         p->acc.stage_calls[r.stage] += 1;
       } else {

@@ -16,6 +16,12 @@ void prof_stage_begin(int stage, cudaStream_t s);
 void prof_stage_end(int stage, cudaStream_t s);
 void prof_gemm_begin(cudaStream_t s);
 void prof_gemm_end(cudaStream_t s, double flops);
+// fine level: every wrapped launch timed and accumulated under its name
+bool prof_fine();
+void prof_launch_begin(cudaStream_t s);
+void prof_launch_end(cudaStream_t s, const char* name);
+void prof_set_fine(Profiler* p, int fine);
+int prof_kernel_summary(Profiler* p, char* buf, size_t len);
 void prof_flush(Profiler* p);  // after the stream is synchronised
 void prof_read(Profiler* p, bse_profile_data* out);
 

@@ -21,6 +21,7 @@
 #include <float.h>
 
 #include "kernels.cuh"
+#include "prof.cuh"
 
 // prm: 0 pivmin, 1 tnorm, 2 twist guard, 3 lower bound, 4 upper bound
 // iprm: 0 number of blocks
@@ -270,19 +271,25 @@ bse_status tridiag_eig(cudaStream_t s, int64_t N, const double* a, const double*
   if (N <= 0) return BSE_OK;
   const int64_t total = mode == 0 ? N : N / 2;
   const int64_t k = iu - il + 1;
+  prof_launch_begin(s);
   tri_prep_kernel<<<1, 1024, 0, s>>>(N, a, off, mode, w.a, w.off, w.e2, w.bstart, w.prm, w.iprm);
+  prof_launch_end(s, "tri_prep_kernel");
   bse_count_launch();
   BSE_LAUNCH_CHECK();
+  prof_launch_begin(s);
   tri_bisect_kernel<<<ceil_div_u(total, 64), 64, 0, s>>>(total, w.a, w.e2, w.bstart, w.iprm, w.prm, mode, w.lam,
                                                          w.blk, status);
+  prof_launch_end(s, "tri_bisect_kernel");
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   tri_rank_kernel<<<ceil_div_u(total, 256), 256, 0, s>>>(total, w.lam, w.iprm, w.rank);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   if (Z) BSE_CUDA(cudaMemset2DAsync(Z, sizeof(double) * ldz, 0, sizeof(double) * N, k, s));
+  prof_launch_begin(s);
   tri_vec_kernel<<<ceil_div_u(total, 64), 64, 0, s>>>(total, il, iu, w.a, w.off, w.e2, w.bstart, w.prm, w.lam,
                                                       w.blk, w.rank, lam_out, Z, ldz, w.scratch, N, status);
+  prof_launch_end(s, "tri_vec_kernel");
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;
