@@ -13,16 +13,16 @@
 //      x = taup (A v - U (Y^H v) - X (V^H v));
 // so that H_L^H A_cur H_R = A_cur - u y^H - x v^H.  The trailing matrix then
 // takes A22 -= U Y^H + X V^H through the GEMM engine.  The two matvecs per
-// step (A^H u: warp per column; A v: thread per row) read the trailing
-// matrix coalesced and are bound by the FP64 pipe on GB300.
+// step (A^H u by column sums, A v by row sums) run over 64 x 64 tiles of the
+// trailing matrix (one CTA per tile, coalesced loads) and are bound by the
+// FP64 pipe on GB300.
 #include "kernels.cuh"
 #include "prof.cuh"
 
 constexpr int NBB = 32;
 constexpr int BRB = 256;
-constexpr int BCH = 512;
 
-static inline int64_t bchunks(int64_t m) { return (m + BCH - 1) / BCH; }
+static inline int64_t bchunks(int64_t m) { return (m + 63) / 64; }  // partial slots (64-wide tiles)
 size_t gebrd_part_elems(int64_t n) { return (size_t)(bchunks(n) + 1) * (size_t)(n + 1) + 4 * (n / BRB + 2) + 64; }
 
 __device__ __forceinline__ double bsum(double v, double* red) {
@@ -125,34 +125,36 @@ __global__ void __launch_bounds__(BRB) bd_house_left(BdArgs a, int nparts) {
   if (r < n) a.U[IDX2(r, i, ld)] = (r == i) ? mkc(1.0, 0.0) : cmul(a.A[IDX2(r, i, a.lda)], hs.scal);
 }
 
-// 1c. part(c) = sum_{r in chunk, r >= i} conj(A(r, c)) u(r), c > i; warp per column
+// 1c. column partials of A^H u over rows >= i, columns > i: 64 x 64 tiles,
+// slot = row block.  Thread (row r, column quarter q) holds 16 entries.
+constexpr int BT64 = 64;
+
 __global__ void __launch_bounds__(BRB) bd_gemv_c(BdArgs a) {
-  __shared__ cplx us[BCH];
+  __shared__ cplx us[BT64];
+  __shared__ cplx cs[4][BT64];
   BD_GUARD();
   const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
-  const int64_t r0 = i + (int64_t)blockIdx.y * BCH, r1 = min(r0 + BCH, n);
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += BRB) us[r - r0] = a.U[IDX2(r, i, ld)];
+  const int64_t r0 = i + (int64_t)blockIdx.y * BT64, c0 = i + 1 + (int64_t)blockIdx.x * BT64;
+  const int tid = threadIdx.x;
+  if (tid < BT64) us[tid] = (r0 + tid < n) ? a.U[IDX2(r0 + tid, i, ld)] : mkc(0.0, 0.0);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c = i + 1 + (int64_t)blockIdx.x * (BRB / 32) + warp;
-  if (c >= n) return;
-  cplx accs[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
-  const cplx* Ac = a.A + IDX2(0, c, a.lda);
-  int64_t r = r0 + lane;
-  for (; r + 96 < r1; r += 128) {
-    cplx av[4];
+  // thread (column c, row quarter q): 16 consecutive rows of one column
+  // (two 128-byte lines, served from L1 after the first touch)
+  const int c = tid & 63, q = tid >> 6;
+  const int64_t gc = c0 + c, rb = r0 + q * 16;
+  cplx av[16];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ac + r + 32 * u);
+  for (int u = 0; u < 16; ++u)
+    av[u] = (gc < n && rb + u < n) ? __ldg(a.A + IDX2(rb + u, gc, a.lda)) : mkc(0.0, 0.0);
+  cplx acc = mkc(0.0, 0.0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) cfma_cj(accs[u], av[u], us[r + 32 * u - r0]);
+  for (int u = 0; u < 16; ++u) cfma_cj(acc, av[u], us[q * 16 + u]);
+  cs[q][c] = acc;
+  __syncthreads();
+  if (tid < BT64) {
+    const int64_t cc = c0 + tid;
+    if (cc < n) a.part[(cc - i - 1) + blockIdx.y * ldp] = cadd(cadd(cs[0][tid], cs[1][tid]), cadd(cs[2][tid], cs[3][tid]));
   }
-  for (; r < r1; r += 32) cfma_cj(accs[0], Ac[r], us[r - r0]);
-  cplx acc = cadd(cadd(accs[0], accs[1]), cadd(accs[2], accs[3]));
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if (lane == 0) a.part[(c - i - 1) + blockIdx.y * ldp] = acc;
 }
 
 // generic small dot: out = sum_{r in [r0, n)} conj(col(r)) vec(r); one CTA per output
@@ -233,28 +235,35 @@ __global__ void __launch_bounds__(BRB) bd_house_right(BdArgs a, int nparts) {
   if (c < n) a.Vr[IDX2(c, i, ld)] = (c == i + 1) ? mkc(1.0, 0.0) : cmul(cconj(a.A[IDX2(i, c, a.lda)]), hs.scal);
 }
 
-// 2c. part(r) = sum_{c in chunk, c > i} A(r, c) v(c), r > i; thread per row
+// 2c. row partials of A v over rows > i, columns > i: 64 x 64 tiles, slot =
+// column block.
 __global__ void __launch_bounds__(BRB) bd_gemv_n(BdArgs a) {
-  __shared__ cplx vs[BCH];
+  __shared__ cplx vs[BT64];
+  __shared__ cplx rs[4][BT64];
   BD_GUARD();
   const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
-  const int64_t c0 = i + 1 + (int64_t)blockIdx.y * BCH, c1 = min(c0 + BCH, n);
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += BRB) vs[c - c0] = a.Vr[IDX2(c, i, ld)];
+  const int64_t r0 = i + 1 + (int64_t)blockIdx.y * BT64, c0 = i + 1 + (int64_t)blockIdx.x * BT64;
+  const int tid = threadIdx.x;
+  if (tid < BT64) vs[tid] = (c0 + tid < n) ? a.Vr[IDX2(c0 + tid, i, ld)] : mkc(0.0, 0.0);
   __syncthreads();
-  const int64_t r = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
-  if (r >= n) return;
-  cplx acc[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
-  const cplx* Ar = a.A + r;
-  int64_t c = c0;
-  for (; c + 3 < c1; c += 4) {
-    cplx av[4];
+  const int r = tid & 63, q = tid >> 6;
+  const int64_t gr = r0 + r;
+  cplx av[16];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ar + (c + u) * a.lda);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) cfma(acc[u], av[u], vs[c + u - c0]);
+  for (int u = 0; u < 16; ++u) {
+    const int64_t gc = c0 + q * 16 + u;
+    av[u] = (gr < n && gc < n) ? __ldg(a.A + IDX2(gr, gc, a.lda)) : mkc(0.0, 0.0);
   }
-  for (; c < c1; ++c) cfma(acc[0], Ar[c * a.lda], vs[c - c0]);
-  a.part[(r - i - 1) + blockIdx.y * ldp] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+  cplx acc = mkc(0.0, 0.0);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) cfma(acc, av[u], vs[q * 16 + u]);
+  rs[q][r] = acc;
+  __syncthreads();
+  if (tid < BT64) {
+    const int64_t rr = r0 + tid;
+    if (rr < n)
+      a.part[(rr - i - 1) + blockIdx.x * ldp] = cadd(cadd(rs[0][tid], rs[1][tid]), cadd(rs[2][tid], rs[3][tid]));
+  }
 }
 
 // 2d. x(r) = taup (sum parts - U s_Y - X s_V), r > i -> X(r, ii)
@@ -310,19 +319,19 @@ bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const Ge
       if (i == n - 1) break;
       const int64_t m = n - i - 1;  // trailing columns / rows
       // y = tauq (A^H u - Y (U^H u) - V (X^H u))
-      dim3 gc(ceil_div_u(m, BRB / 32), (unsigned)bchunks(n - i));
+      dim3 gc(ceil_div_u(m, BT64), ceil_div_u(n - i, BT64));
       BLAUNCH(bd_gemv_c, gc, a);
       if (ii > 0) BLAUNCH(bd_dots, 2 * ii, a, i, ii, w.U, p, ii, w.X, (int64_t)0, w.U + i * ld, w.small);
-      BLAUNCH(bd_y_assemble, ceil_div_u(m, BRB), a, (int)bchunks(n - i));
+      BLAUNCH(bd_y_assemble, ceil_div_u(m, BRB), a, (int)ceil_div_u(n - i, BT64));
       // row update and right reflector
       const unsigned gm = ceil_div_u(m, BRB);
       BLAUNCH(bd_row_update, gm, a);
       BLAUNCH(bd_house_right, gm, a, (int)gm);
       // x = taup (A v - U (Y^H v) - X (V^H v))
-      dim3 gn(ceil_div_u(m, BRB), (unsigned)bchunks(m));
+      dim3 gn(ceil_div_u(m, BT64), ceil_div_u(m, BT64));
       BLAUNCH(bd_gemv_n, gn, a);
       BLAUNCH(bd_dots, 2 * ii + 1, a, i + 1, ii + 1, w.Y, (int64_t)0, ii, w.Vr, p, w.Vr + i * ld, w.small);
-      BLAUNCH(bd_x_assemble, gm, a, (int)bchunks(m));
+      BLAUNCH(bd_x_assemble, gm, a, (int)ceil_div_u(m, BT64));
     }
     const int64_t t0 = p + bs, mt = n - t0;
     if (mt > 0) {

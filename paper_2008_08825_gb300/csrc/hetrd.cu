@@ -9,7 +9,7 @@
 //   2. gets the reflector H_j = I - tau v v^H with H_j^H x = beta e_1,
 //      beta real (tr_house), so T is real,
 //   3. w = tau (A22 v - V (W^H v) - W (V^H v)) with A22 v from the lower
-//      triangle in two coalesced passes (tr_hemv_lo, tr_hemv_up),
+//      triangle, 64 x 64 tiles, each tile read once (tr_hemv_tiled),
 //   4. w += -tau/2 (w^H v) v  -- so that H_j^H A H_j = A - v w^H - w v^H.
 // After the panel, the trailing lower triangle takes the rank-2*NBT update
 // through the GEMM engine.  On GB300 step 3 is bound by the FP64 pipe, not by
@@ -27,7 +27,10 @@ constexpr int BTB = 128;   // reflectors per block in the back-transformation
 int hetrd_panel() { return NBT; }
 int backtransform_block() { return BTB; }
 static inline int64_t nchunks(int64_t m) { return (m + HCH - 1) / HCH; }
-size_t hetrd_part_elems(int64_t n) { return (size_t)(2 * nchunks(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64; }
+size_t hetrd_part_elems(int64_t n) {
+  const int64_t slots = (n + 63) / 64 > 2 * nchunks(n) ? (n + 63) / 64 : 2 * nchunks(n);
+  return (size_t)(slots + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64;
+}
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -126,73 +129,86 @@ __global__ void __launch_bounds__(RB) tr_house(int64_t n, int64_t j, const cplx*
   if (r < n) V[IDX2(r, j, ldv)] = (r == j + 1) ? mkc(1.0, 0.0) : cmul(A[IDX2(r, j, lda)], hs.scal);
 }
 
-// 3a. y1(r) = sum_{j+1 <= c <= r} A(r, c) v(c), partial over column chunks
-__global__ void __launch_bounds__(RB) tr_hemv_lo(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
-                                                 const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
-                                                 int64_t ldpart, const int64_t* status) {
-  __shared__ cplx vs[HCH];
-  if (*(volatile const int64_t*)status) return;
-  const int64_t base = j + 1;
-  const int64_t m = n - base;
-  const int64_t c0 = (int64_t)blockIdx.y * HCH;
-  const int64_t rb0 = (int64_t)blockIdx.x * RB;
-  const int64_t rmax = rb0 + RB - 1;
-  const int64_t r = rb0 + threadIdx.x;  // local row
-  if (c0 > rmax) {                      // chunk entirely above this row block
-    if (r < m) part[r + blockIdx.y * ldpart] = mkc(0.0, 0.0);
-    return;
-  }
-  const int64_t c1 = min(c0 + HCH, m);
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += RB) vs[c - c0] = V[IDX2(base + c, j, ldv)];
-  __syncthreads();
-  if (r >= m) return;
-  const int64_t cend = min(c1, r + 1);
-  cplx acc[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
-  const cplx* Ar = A + IDX2(base + r, base, lda);
-  int64_t c = c0;
-  for (; c + 3 < cend; c += 4) {
-    cplx av[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ar + (c + u) * lda);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) cfma(acc[u], av[u], vs[c + u - c0]);
-  }
-  for (; c < cend; ++c) cfma(acc[0], Ar[c * lda], vs[c - c0]);
-  part[r + blockIdx.y * ldpart] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+// 3. y = A22 v from the lower triangle in 64 x 64 tiles, one CTA per tile of
+// the lower triangle: each tile is read once and gives both its row sums
+// (A v) and, off the diagonal, its column sums (A^H v).  Slot s of the
+// partial buffer for an index i in block b is written by exactly one tile:
+// (b, s) for s < b (row sums), (b, b) (row sums + strict-lower column
+// sums), (s, b) for s > b (column sums); the assembly adds the slots.
+constexpr int HT = 64;
+constexpr int HEMV_SMEM = (int)sizeof(cplx) * HT * (HT + 1);  // 66,560 bytes of dynamic shared memory
+
+__device__ __forceinline__ void tile_of(int64_t L, int64_t* bi, int64_t* bj) {
+  int64_t b = (int64_t)((sqrt(8.0 * (double)L + 1.0) - 1.0) * 0.5);
+  while ((b + 1) * (b + 2) / 2 <= L) ++b;
+  while (b * (b + 1) / 2 > L) --b;
+  *bi = b;
+  *bj = L - b * (b + 1) / 2;
 }
 
-// 3b. y2(c) = sum_{r > c} conj(A(r, c)) v(r), warp per column, partial over row chunks
-__global__ void __launch_bounds__(RB) tr_hemv_up(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
-                                                 const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
-                                                 int64_t ldpart, const int64_t* status) {
-  __shared__ cplx vs[HCH];
+__global__ void __launch_bounds__(256) tr_hemv_tiled(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
+                                                     const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
+                                                     int64_t ldpart, const int64_t* status) {
+  extern __shared__ cplx T[];  // column partials, T[c * (HT + 1) + r]
+  __shared__ cplx vr[HT], vc[HT];
+  __shared__ cplx rs[4][HT];
+  __shared__ cplx cs[4][HT];
   if (*(volatile const int64_t*)status) return;
-  const int64_t base = j + 1;
-  const int64_t m = n - base;
-  const int64_t r0 = (int64_t)blockIdx.y * HCH;
-  const int64_t r1 = min(r0 + HCH, m);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c = (int64_t)blockIdx.x * (RB / 32) + warp;  // local column
-  for (int64_t rr = r0 + threadIdx.x; rr < r1; rr += RB) vs[rr - r0] = V[IDX2(base + rr, j, ldv)];
+  const int64_t base = j + 1, m = n - base;
+  int64_t bi, bj;
+  tile_of(blockIdx.x, &bi, &bj);
+  const int64_t r0 = bi * HT, c0 = bj * HT;
+  const int tid = threadIdx.x;
+  if (tid < HT) {
+    vr[tid] = (r0 + tid < m) ? V[IDX2(base + r0 + tid, j, ldv)] : mkc(0.0, 0.0);
+    vc[tid] = (c0 + tid < m) ? V[IDX2(base + c0 + tid, j, ldv)] : mkc(0.0, 0.0);
+  }
   __syncthreads();
-  if (c >= m) return;
-  cplx accs[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
-  const cplx* Ac = A + IDX2(base, base + c, lda);
-  int64_t rr = max(r0, c + 1) + lane;
-  for (; rr + 96 < r1; rr += 128) {
-    cplx av[4];
+  // load: thread (row r, column quarter q), coalesced along rows
+  const int r = tid & 63, q = tid >> 6;
+  const int64_t gr = r0 + r;
+  const bool diag = bi == bj;
+  const cplx* Ar = A + IDX2(base + gr, base + c0, lda);
+  cplx av[16];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) av[u] = __ldg(Ac + rr + 32 * u);
+  for (int u = 0; u < 16; ++u) {
+    const int c = q * 16 + u;
+    const bool in = gr < m && c0 + c < m && (!diag || r >= c);
+    av[u] = in ? __ldg(Ar + (int64_t)c * lda) : mkc(0.0, 0.0);
+  }
+  const cplx vrr = vr[r];
+  cplx rowacc = mkc(0.0, 0.0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) cfma_cj(accs[u], av[u], vs[rr + 32 * u - r0]);
+  for (int u = 0; u < 16; ++u) {
+    const int c = q * 16 + u;
+    cfma(rowacc, av[u], vc[c]);
+    cplx t = mkc(0.0, 0.0);
+    if (!diag || r > c) cfma_cj(t, av[u], vrr);
+    T[c * (HT + 1) + r] = t;
   }
-  for (; rr < r1; rr += 32) cfma_cj(accs[0], Ac[rr], vs[rr - r0]);
-  cplx acc = cadd(cadd(accs[0], accs[1]), cadd(accs[2], accs[3]));
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  rs[q][r] = rowacc;
+  __syncthreads();
+  // column sums: thread (column c, row quarter q) adds 16 staged partials
+  {
+    const int c = tid & 63;
+    cplx acc = mkc(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc = cadd(acc, T[c * (HT + 1) + q * 16 + u]);
+    cs[q][c] = acc;
   }
-  if (lane == 0) part[c + blockIdx.y * ldpart] = acc;
+  __syncthreads();
+  if (tid < HT) {
+    const int64_t i = r0 + tid;
+    if (i < m) {
+      cplx y = cadd(cadd(rs[0][tid], rs[1][tid]), cadd(rs[2][tid], rs[3][tid]));
+      if (diag) y = cadd(y, cadd(cadd(cs[0][tid], cs[1][tid]), cadd(cs[2][tid], cs[3][tid])));
+      part[i + bj * ldpart] = y;
+    }
+  } else if (tid < 2 * HT && !diag) {
+    const int c = tid - HT;
+    const int64_t i = c0 + c;
+    if (i < m) part[i + bi * ldpart] = cadd(cadd(cs[0][c], cs[1][c]), cadd(cs[2][c], cs[3][c]));
+  }
 }
 
 // 3c. s1 = W^H v, s2 = V_panel^H v over rows >= j+1 (one CTA per output)
@@ -230,10 +246,7 @@ __global__ void __launch_bounds__(RB) tr_w_assemble(int64_t n, int64_t p, int64_
   cplx dot = mkc(0.0, 0.0);
   if (r < m) {
     cplx y = mkc(0.0, 0.0);
-    for (int c = 0; c < nch; ++c) {
-      y = cadd(y, part[r + c * ldpart]);
-      y = cadd(y, part[r + (nch + c) * ldpart]);
-    }
+    for (int c = 0; c < nch; ++c) y = cadd(y, part[r + c * ldpart]);
     const int64_t gr = base + r;
     for (int q = 0; q < jj; ++q) {
       y = csub(y, cmul(V[IDX2(gr, p + q, ldv)], s1[q]));
@@ -285,11 +298,17 @@ __global__ void tr_last_diag(int64_t n, const cplx* A, int64_t lda, double* d, c
 bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const HetrdWork& w,
                        const int64_t* status) {
   if (n <= 0) return BSE_OK;
+  static bool attr = false;
+  if (!attr) {
+    BSE_CUDA(cudaFuncSetAttribute(tr_hemv_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, HEMV_SMEM));
+    attr = true;
+  }
   const int64_t ldv = n, ldw = n;
   BSE_CUDA(cudaMemsetAsync(w.V, 0, sizeof(cplx) * n * n, s));
   const int64_t ldpart = n + 1;
   cplx* part = w.part;                                     // 2 * nchunks columns of length ldpart
-  double* npart = (double*)(w.part + 2 * nchunks(n) * ldpart);
+  const int64_t slots = (n + 63) / 64 > 2 * nchunks(n) ? (n + 63) / 64 : 2 * nchunks(n);
+  double* npart = (double*)(w.part + slots * ldpart);
   double* dpart = npart + (n / RB + 2);
   cplx* s12 = w.small;
   const cplx one = mkc(1.0, 0.0), mone = mkc(-1.0, 0.0);
@@ -301,11 +320,16 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       LAUNCH(tr_col_update, g1, RB, n, p, j, A, lda, w.V, ldv, w.W, ldw, w.d, npart, status);
       const unsigned g2 = ceil_div_u(m, RB);
       LAUNCH(tr_house, g2, RB, n, j, A, lda, w.V, ldv, w.tau, w.e, npart, (int)g1, status);
-      const int64_t nch = nchunks(m);
-      dim3 glo(ceil_div_u(m, RB), (unsigned)nch);
-      LAUNCH(tr_hemv_lo, glo, RB, n, j, A, lda, w.V, ldv, part, ldpart, status);
-      dim3 gup(ceil_div_u(m, RB / 32), (unsigned)nch);
-      LAUNCH(tr_hemv_up, gup, RB, n, j, A, lda, w.V, ldv, part + nch * ldpart, ldpart, status);
+      const int64_t nt = (m + HT - 1) / HT;  // tile rows; partial slots
+      {
+        prof_launch_begin(s);
+        tr_hemv_tiled<<<(unsigned)(nt * (nt + 1) / 2), RB, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart,
+                                                                            status);
+        prof_launch_end(s, "tr_hemv_tiled");
+        bse_count_launch();
+        BSE_LAUNCH_CHECK();
+      }
+      const int64_t nch = nt;
       const int jj = (int)(j - p);
       if (jj > 0) LAUNCH(tr_panel_dots, 2 * jj, RB, n, p, j, w.V, ldv, w.W, ldw, s12, status);
       LAUNCH(tr_w_assemble, g2, RB, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, s12, w.tau, dpart,

@@ -208,8 +208,10 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                : "r"(addr));
 }
 
+// not volatile: ordered by its data dependences only, so the scheduler can
+// overlap the next ldmatrix with the MMAs in flight
 __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -220,8 +222,16 @@ template <int S>
 __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
   extern __shared__ __align__(128) unsigned char osm[];
   const GemmParams<cplx>& p = z.p;
-  const int64_t i0 = (int64_t)blockIdx.y * OZ_BM;        // real rows = complex rows
-  const int64_t jr0 = (int64_t)blockIdx.x * OZ_BN;       // real columns
+  // grouped rasterisation: consecutive CTAs walk down groups of 8 tile rows so
+  // that the slices of 8 row panels and of a few column panels stay in L2
+  const int64_t gx = gridDim.x, gy = gridDim.y;
+  const int64_t lin = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gx;
+  const int64_t grp = lin / (8 * gx), first = grp * 8;
+  const int64_t rows = (gy - first) < 8 ? (gy - first) : 8;
+  const int64_t loc = lin % (8 * gx);
+  const int64_t ty = first + loc % rows, tx = loc / rows;
+  const int64_t i0 = ty * OZ_BM;                         // real rows = complex rows
+  const int64_t jr0 = tx * OZ_BN;                        // real columns
   const int64_t jc0 = jr0 / 2;                           // complex columns
   if (i0 >= p.m || jc0 >= p.n) return;
   if (p.lowerC && jc0 > i0 + OZ_BM - 1) return;
@@ -292,22 +302,23 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
           const int col = ks * 16 + (lane >> 4) * 8;  // bf16 index
           ldsm_x4(abase + row * OZ_ROWB + col * 2, a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
         }
+        const int nrow = wn * 16 + (lane & 7) + (lane >> 4) * 8;
+        const int kcol = ks * 16 + ((lane >> 3) & 1) * 8;
+        const uint32_t boff = nrow * OZ_ROWB + kcol * 2;
+        uint32_t bc[4], bn[4];
+        ldsm_x4(st + S * SLICE_BYTES + boff, bc[0], bc[1], bc[2], bc[3]);
 #pragma unroll
         for (int u = 0; u < S - t; ++u) {  // u index 0-based: level (t+1)+(u+1) = t + u + 2 <= S + 1
-          const uint32_t bbase = st + (S + u) * SLICE_BYTES;
-          const int nrow = wn * 16 + (lane & 7) + (lane >> 4) * 8;
-          const int kcol = ks * 16 + ((lane >> 3) & 1) * 8;
-          uint32_t b0, b1, b2, b3;
-          ldsm_x4(bbase + nrow * OZ_ROWB + kcol * 2, b0, b1, b2, b3);
-          constexpr int dummy = 0;
-          (void)dummy;
+          if (u + 1 < S - t) ldsm_x4(st + (S + u + 1) * SLICE_BYTES + boff, bn[0], bn[1], bn[2], bn[3]);
           const int lev = t + u;  // 0-based level (l - 2)
           const int set = lev < OZ_NSETS - 1 ? lev : OZ_NSETS - 1;
 #pragma unroll
           for (int mi = 0; mi < 2; ++mi) {
-            mma_bf16(&acc[set][(mi * 2 + 0) * 4], a[mi], b0, b1);
-            mma_bf16(&acc[set][(mi * 2 + 1) * 4], a[mi], b2, b3);
+            mma_bf16(&acc[set][(mi * 2 + 0) * 4], a[mi], bc[0], bc[1]);
+            mma_bf16(&acc[set][(mi * 2 + 1) * 4], a[mi], bc[2], bc[3]);
           }
+#pragma unroll
+          for (int x = 0; x < 4; ++x) bc[x] = bn[x];
         }
       }
     }
