@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=768)
     ap.add_argument("--methods", default="chol,svd", help="comma list of chol, svd")
     ap.add_argument("--precisions", default="fp64,mixed", help="fp64 (headline) and/or mixed")
+    ap.add_argument("--kernel-profile", action="store_true",
+                    help="instead of timing steps: one warm solve per method and precision with per-kernel "
+                         "event profiling (library profiling level 2), one JSON line each")
     ap.add_argument("--workload", default="n8192", choices=["n8192", "batched"],
                     help="n8192: the headline solve; batched: 512 uneven instances, lowest 32 pairs")
     return ap.parse_args()
@@ -209,6 +212,35 @@ def run_batched(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_kernel_profile(args, local):
+    import torch
+
+    from paper_2008_08825_gb300 import bse, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    A, B = inputs.base(args.n, seed=0)
+    At, Bt = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    h = bse.Handle()
+    names = ["form", "cholesky", "congruence_or_product", "householder_reduction", "tridiagonal",
+             "orthogonalisation", "back_transformation", "post_processing", "gradient", "refinement"]
+    for prec in [q for q in args.precisions.split(",") if q]:
+        for m in [x for x in args.methods.split(",") if x]:
+            bse.solve(At, Bt, method=m, precision=prec, handle=h)
+            torch.cuda.synchronize()
+            bse.lib().bse_profile_enable(h.ptr, 2)
+            bse.solve(At, Bt, method=m, precision=prec, handle=h)
+            torch.cuda.synchronize()
+            pr = _read_profile(bse, h)
+            kp = h.kernel_profile()
+            bse.lib().bse_profile_enable(h.ptr, 0)
+            print(json.dumps({"n": args.n, "method": m, "precision": prec,
+                              "stage_ms": {k: v for k, v in zip(names, pr["stage_ms"]) if v > 0},
+                              "gemm_ms": pr["gemm_ms"], "gemm_launches": pr["gemm_launches"],
+                              "gemm_fp64_equiv_tflops": pr["gemm_flops"] / max(pr["gemm_ms"], 1e-9) / 1e9,
+                              "kernels": {k: {"launches": c, "ms": t} for k, (c, t) in kp.items()}}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -219,6 +251,9 @@ def main():
         import numpy as np  # noqa: F401
 
         run_batched(args, rank, world, local)
+        return
+    if args.kernel_profile:
+        run_kernel_profile(args, local)
         return
     import numpy as np
     import torch

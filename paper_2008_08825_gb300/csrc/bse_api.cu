@@ -106,6 +106,7 @@ struct TriPlan {
     w.E = pl.take<double>((size_t)k * k);
     w.Ef = pl.take<float>((size_t)k * k);
     w.Z2 = pl.take<double>((size_t)N * k);
+    w.grid = pl.take<int>(tri_grid_points());
   }
 };
 
@@ -648,7 +649,8 @@ bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t
 bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, int64_t lda, const double* B,
                           int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx,
                           double* Y, int64_t ldy, bse_info* info, void* stream) {
-  if (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
+  if (method == BSE_METHOD_SVD) return bse_internal_set_error("batched SVD method is not available in this build"), BSE_ERR_NOT_IMPLEMENTED;
+  if (method != BSE_METHOD_CHOL) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
   bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
   if (r != BSE_OK || n == 0) return r;
   cudaStream_t s = (cudaStream_t)stream;

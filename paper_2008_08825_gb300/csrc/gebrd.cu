@@ -174,23 +174,34 @@ __global__ void __launch_bounds__(BRB) bd_dots(BdArgs a, int64_t r0, int nA, con
   (void)nB;
 }
 
-// 1d. y(c) = tauq (sum parts - Y s_U - V s_X), c > i -> Y(c, ii)
+// 1d. y(c) = tauq (sum parts - Y s_U - V s_X), c > i -> Y(c, ii); 64 entries
+// per CTA, 4 threads per entry
+constexpr int AR = 64;
+
 __global__ void __launch_bounds__(BRB) bd_y_assemble(BdArgs a, int nch) {
   __shared__ cplx su[NBB], sx[NBB];
+  __shared__ cplx red4[4][AR];
   BD_GUARD();
   const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
   const int ii = (int)(i - a.p);
   if (threadIdx.x < ii) su[threadIdx.x] = a.s[threadIdx.x], sx[threadIdx.x] = a.s[NBB + threadIdx.x];
   __syncthreads();
-  const int64_t c = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
-  if (c >= n) return;
+  const int rl = threadIdx.x & (AR - 1), qq = threadIdx.x / AR;
+  const int64_t c = i + 1 + (int64_t)blockIdx.x * AR + rl;
   cplx y = mkc(0.0, 0.0);
-  for (int k = 0; k < nch; ++k) y = cadd(y, a.part[(c - i - 1) + k * ldp]);
-  for (int q = 0; q < ii; ++q) {
-    y = csub(y, cmul(a.Y[IDX2(c, q, ld)], su[q]));
-    y = csub(y, cmul(a.Vr[IDX2(c, a.p + q, ld)], sx[q]));
+  if (c < n) {
+    for (int k = qq; k < nch; k += 4) y = cadd(y, a.part[(c - i - 1) + k * ldp]);
+    for (int q = qq; q < ii; q += 4) {
+      y = csub(y, cmul(a.Y[IDX2(c, q, ld)], su[q]));
+      y = csub(y, cmul(a.Vr[IDX2(c, a.p + q, ld)], sx[q]));
+    }
   }
-  a.Y[IDX2(c, ii, ld)] = cmul(a.tauq[i], y);
+  red4[qq][rl] = y;
+  __syncthreads();
+  if (qq == 0 && c < n) {
+    y = cadd(cadd(red4[0][rl], red4[1][rl]), cadd(red4[2][rl], red4[3][rl]));
+    a.Y[IDX2(c, ii, ld)] = cmul(a.tauq[i], y);
+  }
 }
 
 // 2a. row update (c > i), partial norms of c >= i+2
@@ -266,22 +277,31 @@ __global__ void __launch_bounds__(BRB) bd_gemv_n(BdArgs a) {
   }
 }
 
-// 2d. x(r) = taup (sum parts - U s_Y - X s_V), r > i -> X(r, ii)
+// 2d. x(r) = taup (sum parts - U s_Y - X s_V), r > i -> X(r, ii); 64 rows per
+// CTA, 4 threads per row
 __global__ void __launch_bounds__(BRB) bd_x_assemble(BdArgs a, int nch) {
   __shared__ cplx sy[NBB], sv[NBB];
+  __shared__ cplx red4[4][AR];
   BD_GUARD();
   const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
   const int ii = (int)(i - a.p);
   if (threadIdx.x <= ii) sy[threadIdx.x] = a.s[threadIdx.x];
   if (threadIdx.x < ii) sv[threadIdx.x] = a.s[NBB + threadIdx.x];
   __syncthreads();
-  const int64_t r = i + 1 + (int64_t)blockIdx.x * BRB + threadIdx.x;
-  if (r >= n) return;
+  const int rl = threadIdx.x & (AR - 1), qq = threadIdx.x / AR;
+  const int64_t r = i + 1 + (int64_t)blockIdx.x * AR + rl;
   cplx x = mkc(0.0, 0.0);
-  for (int k = 0; k < nch; ++k) x = cadd(x, a.part[(r - i - 1) + k * ldp]);
-  for (int q = 0; q <= ii; ++q) x = csub(x, cmul(a.U[IDX2(r, a.p + q, ld)], sy[q]));
-  for (int q = 0; q < ii; ++q) x = csub(x, cmul(a.X[IDX2(r, q, ld)], sv[q]));
-  a.X[IDX2(r, ii, ld)] = cmul(a.taup[i], x);
+  if (r < n) {
+    for (int k = qq; k < nch; k += 4) x = cadd(x, a.part[(r - i - 1) + k * ldp]);
+    for (int q = qq; q <= ii; q += 4) x = csub(x, cmul(a.U[IDX2(r, a.p + q, ld)], sy[q]));
+    for (int q = qq; q < ii; q += 4) x = csub(x, cmul(a.X[IDX2(r, q, ld)], sv[q]));
+  }
+  red4[qq][rl] = x;
+  __syncthreads();
+  if (qq == 0 && r < n) {
+    x = cadd(cadd(red4[0][rl], red4[1][rl]), cadd(red4[2][rl], red4[3][rl]));
+    a.X[IDX2(r, ii, ld)] = cmul(a.taup[i], x);
+  }
 }
 
 #define BLAUNCH(kern, grid, ...)                 \
@@ -322,7 +342,7 @@ bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const Ge
       dim3 gc(ceil_div_u(m, BT64), ceil_div_u(n - i, BT64));
       BLAUNCH(bd_gemv_c, gc, a);
       if (ii > 0) BLAUNCH(bd_dots, 2 * ii, a, i, ii, w.U, p, ii, w.X, (int64_t)0, w.U + i * ld, w.small);
-      BLAUNCH(bd_y_assemble, ceil_div_u(m, BRB), a, (int)ceil_div_u(n - i, BT64));
+      BLAUNCH(bd_y_assemble, ceil_div_u(m, AR), a, (int)ceil_div_u(n - i, BT64));
       // row update and right reflector
       const unsigned gm = ceil_div_u(m, BRB);
       BLAUNCH(bd_row_update, gm, a);
@@ -331,7 +351,7 @@ bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const Ge
       dim3 gn(ceil_div_u(m, BT64), ceil_div_u(m, BT64));
       BLAUNCH(bd_gemv_n, gn, a);
       BLAUNCH(bd_dots, 2 * ii + 1, a, i + 1, ii + 1, w.Y, (int64_t)0, ii, w.Vr, p, w.Vr + i * ld, w.small);
-      BLAUNCH(bd_x_assemble, gm, a, (int)ceil_div_u(m, BT64));
+      BLAUNCH(bd_x_assemble, ceil_div_u(m, AR), a, (int)ceil_div_u(m, BT64));
     }
     const int64_t t0 = p + bs, mt = n - t0;
     if (mt > 0) {

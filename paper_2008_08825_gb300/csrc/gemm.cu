@@ -96,5 +96,15 @@ bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
   }
   return gemm_launch<cplx, 8>(s, p);
 }
-bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) { return gemm_launch<double, 16>(s, p); }
+bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) {
+  const OzWork oz = oz_current();
+  if (oz.ptr && p.opA != OPC && p.opB != OPC && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
+    const bool prof = prof_current() != nullptr;
+    if (prof) prof_gemm_begin(s);
+    const bse_status r = gemm_d_oz_raw(s, p);
+    if (prof) prof_gemm_end(s, useful_macs(p) * 2.0);
+    return r;
+  }
+  return gemm_launch<double, 16>(s, p);
+}
 bse_status gemm_f(cudaStream_t s, const GemmParams<float>& p) { return gemm_launch<float, 32>(s, p); }

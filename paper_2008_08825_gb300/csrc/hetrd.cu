@@ -20,7 +20,7 @@
 #include "prof.cuh"
 
 constexpr int NBT = 32;    // panel width
-constexpr int RB = 256;    // rows per CTA in column kernels
+constexpr int RB = 64;     // rows per CTA (and threads) of the per-column row kernels
 constexpr int HCH = 512;   // column chunk of the Hermitian matvec
 constexpr int BTB = 128;   // reflectors per block in the back-transformation
 
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) tr_hemv_tiled(int64_t n, int64_t j, const
 }
 
 // 3c. s1 = W^H v, s2 = V_panel^H v over rows >= j+1 (one CTA per output)
-__global__ void __launch_bounds__(RB) tr_panel_dots(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
+__global__ void __launch_bounds__(256) tr_panel_dots(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
                                                     int64_t ldv, const cplx* __restrict__ W, int64_t ldw,
                                                     cplx* __restrict__ s12, const int64_t* status) {
   __shared__ double red[32];
@@ -221,18 +221,22 @@ __global__ void __launch_bounds__(RB) tr_panel_dots(int64_t n, int64_t p, int64_
   const int q = blockIdx.x % jj, which = blockIdx.x / jj;  // which 0: W, 1: V
   const cplx* col = which == 0 ? W + IDX2(0, q, ldw) : V + IDX2(0, p + q, ldv);
   cplx acc = mkc(0.0, 0.0);
-  for (int64_t r = j + 1 + threadIdx.x; r < n; r += RB) cfma_cj(acc, col[r], V[IDX2(r, j, ldv)]);
+  for (int64_t r = j + 1 + threadIdx.x; r < n; r += blockDim.x) cfma_cj(acc, col[r], V[IDX2(r, j, ldv)]);
   const cplx s = block_sum_c(acc, red);
   if (threadIdx.x == 0) s12[which * NBT + q] = s;
 }
 
-// 3d. w = tau (y1 + y2 - V s1 - W s2), stored in W(:, jj); partial sums of w^H v
-__global__ void __launch_bounds__(RB) tr_w_assemble(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
-                                                    int64_t ldv, cplx* __restrict__ W, int64_t ldw,
-                                                    const cplx* __restrict__ part, int64_t ldpart, int nch,
-                                                    const cplx* __restrict__ s12, const cplx* __restrict__ tau,
-                                                    double* __restrict__ dpart, const int64_t* status) {
+// 3d. w = tau (y - V s1 - W s2), stored in W(:, jj); partial sums of w^H v.
+// 64 rows per CTA, 4 threads per row (slots and panel columns split 4 ways).
+constexpr int AR = 64;
+
+__global__ void __launch_bounds__(256) tr_w_assemble(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
+                                                     int64_t ldv, cplx* __restrict__ W, int64_t ldw,
+                                                     const cplx* __restrict__ part, int64_t ldpart, int nch,
+                                                     const cplx* __restrict__ s12, const cplx* __restrict__ tau,
+                                                     double* __restrict__ dpart, const int64_t* status) {
   __shared__ cplx s1[NBT], s2[NBT];
+  __shared__ cplx red4[4][AR];
   __shared__ double red[32];
   if (*(volatile const int64_t*)status) return;
   const int jj = (int)(j - p);
@@ -242,24 +246,31 @@ __global__ void __launch_bounds__(RB) tr_w_assemble(int64_t n, int64_t p, int64_
   }
   __syncthreads();
   const int64_t base = j + 1, m = n - base;
-  const int64_t r = (int64_t)blockIdx.x * RB + threadIdx.x;
-  cplx dot = mkc(0.0, 0.0);
+  const int rl = threadIdx.x & (AR - 1), qq = threadIdx.x / AR;
+  const int64_t r = (int64_t)blockIdx.x * AR + rl;
+  cplx y = mkc(0.0, 0.0);
   if (r < m) {
-    cplx y = mkc(0.0, 0.0);
-    for (int c = 0; c < nch; ++c) y = cadd(y, part[r + c * ldpart]);
+    for (int c = qq; c < nch; c += 4) y = cadd(y, part[r + c * ldpart]);
     const int64_t gr = base + r;
-    for (int q = 0; q < jj; ++q) {
+    for (int q = qq; q < jj; q += 4) {
       y = csub(y, cmul(V[IDX2(gr, p + q, ldv)], s1[q]));
       y = csub(y, cmul(W[IDX2(gr, q, ldw)], s2[q]));
     }
+  }
+  red4[qq][rl] = y;
+  __syncthreads();
+  cplx dot = mkc(0.0, 0.0);
+  if (qq == 0 && r < m) {
+    y = cadd(cadd(red4[0][rl], red4[1][rl]), cadd(red4[2][rl], red4[3][rl]));
     y = cmul(tau[j], y);
+    const int64_t gr = base + r;
     W[IDX2(gr, jj, ldw)] = y;
     dot = cmul(cconj(y), V[IDX2(gr, j, ldv)]);
   }
-  const cplx s = block_sum_c(dot, red);
+  const cplx sdot = block_sum_c(dot, red);
   if (threadIdx.x == 0) {
-    dpart[2 * blockIdx.x] = s.x;
-    dpart[2 * blockIdx.x + 1] = s.y;
+    dpart[2 * blockIdx.x] = sdot.x;
+    dpart[2 * blockIdx.x + 1] = sdot.y;
   }
 }
 
@@ -323,7 +334,7 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       const int64_t nt = (m + HT - 1) / HT;  // tile rows; partial slots
       {
         prof_launch_begin(s);
-        tr_hemv_tiled<<<(unsigned)(nt * (nt + 1) / 2), RB, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart,
+        tr_hemv_tiled<<<(unsigned)(nt * (nt + 1) / 2), 256, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart,
                                                                             status);
         prof_launch_end(s, "tr_hemv_tiled");
         bse_count_launch();
@@ -331,10 +342,11 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       }
       const int64_t nch = nt;
       const int jj = (int)(j - p);
-      if (jj > 0) LAUNCH(tr_panel_dots, 2 * jj, RB, n, p, j, w.V, ldv, w.W, ldw, s12, status);
-      LAUNCH(tr_w_assemble, g2, RB, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, s12, w.tau, dpart,
+      if (jj > 0) LAUNCH(tr_panel_dots, 2 * jj, 256, n, p, j, w.V, ldv, w.W, ldw, s12, status);
+      const unsigned ga = ceil_div_u(m, AR);
+      LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, s12, w.tau, dpart,
              status);
-      LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)g2, status);
+      LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)ga, status);
     }
     const int64_t t0 = p + bs, mt = n - t0;
     if (mt > 0) {

@@ -76,7 +76,9 @@ struct TriWork {
   double* E;       // kmax * kmax (orthogonalisation Gram matrix)
   float* Ef;       // kmax * kmax
   double* Z2;      // N * kmax doubles (also holds two N * kmax float arrays)
+  int* grid;       // tri_grid_points() Sturm counts
 };
+int tri_grid_points();
 // mode 0: all N eigenvalues of T.  mode 1 (Golub-Kahan form, zero diagonal,
 // even N): the N/2 positive eigenvalues (the upper half of each block).
 // Selected ascending indices [il, iu] (0-based, inclusive) of the computed set.
@@ -131,3 +133,4 @@ void oz_set_current(const OzWork& w);
 OzWork oz_current();
 size_t oz_work_bytes(int64_t maxdim, int slices);
 bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p);
+bse_status gemm_d_oz_raw(cudaStream_t s, const GemmParams<double>& p);

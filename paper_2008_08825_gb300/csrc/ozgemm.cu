@@ -186,8 +186,9 @@ __global__ void oz_split_b_kernel(int64_t k, int64_t n, const cplx* B, int64_t l
 }
 
 // ---- the tensor-core product -------------------------------------------------
+template <typename T>
 struct OzArgs {
-  GemmParams<cplx> p;
+  GemmParams<T> p;
   const uint32_t* As;
   const uint32_t* Bs;
   const int* ea;
@@ -218,10 +219,14 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int S>
-__global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
+// T = cplx: complex product through the real 2x2 embedding (k' = 2k, two
+// real columns per complex column); T = double: real product (k' = k).
+template <int S, typename T>
+__global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs<T> z) {
   extern __shared__ __align__(128) unsigned char osm[];
-  const GemmParams<cplx>& p = z.p;
+  constexpr bool CPLX = sizeof(T) == sizeof(cplx);
+  constexpr int XF = CPLX ? 2 : 1;  // real rows/cols of k' and n' per logical index
+  const GemmParams<T>& p = z.p;
   // grouped rasterisation: consecutive CTAs walk down groups of 8 tile rows so
   // that the slices of 8 row panels and of a few column panels stay in L2
   const int64_t gx = gridDim.x, gy = gridDim.y;
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
   const int64_t ty = first + loc % rows, tx = loc / rows;
   const int64_t i0 = ty * OZ_BM;                         // real rows = complex rows
   const int64_t jr0 = tx * OZ_BN;                        // real columns
-  const int64_t jc0 = jr0 / 2;                           // complex columns
+  const int64_t jc0 = jr0 / XF;                          // logical columns
   if (i0 >= p.m || jc0 >= p.n) return;
   if (p.lowerC && jc0 > i0 + OZ_BM - 1) return;
   if (p.status && *(volatile const int64_t*)p.status) return;
@@ -241,8 +246,8 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
   if (p.triA == TRI_LO) ke = min(ke, i0 + OZ_BM);
   if (p.triA == TRI_UP) kb = max(kb, i0);
   if (p.triB == TRI_LO) kb = max(kb, jc0);
-  if (p.triB == TRI_UP) ke = min(ke, jc0 + OZ_BN / 2);
-  int64_t kb2 = (2 * kb / OZ_BK) * OZ_BK, ke2 = 2 * ke;
+  if (p.triB == TRI_UP) ke = min(ke, jc0 + OZ_BN / XF);
+  int64_t kb2 = (XF * kb / OZ_BK) * OZ_BK, ke2 = XF * ke;
   const int64_t ntile = ke2 > kb2 ? (ke2 - kb2 + OZ_BK - 1) / OZ_BK : 0;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -335,38 +340,137 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs z) {
   }
   cp_wait0();
 
-  // epilogue: (c0, c1) / (c2, c3) of tile (mi, ni) are Re/Im of one entry
-  const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
+  // epilogue: complex -- (c0, c1) / (c2, c3) of tile (mi, ni) are Re/Im of
+  // one entry; real -- they are two adjacent columns
+  if constexpr (CPLX) {
+    const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+    for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-    for (int ni = 0; ni < 2; ++ni)
+      for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t i = i0 + wm * 32 + mi * 16 + g + 8 * h;
-        const int64_t j = jc0 + wn * 8 + ni * 4 + tg;
-        if (i >= p.m || j >= p.n) continue;
-        if (p.lowerC && i < j) continue;
-        const int q = (mi * 2 + ni) * 4 + 2 * h;
-        const int ei = z.ea[i], fj = z.fb[j];
-        double re = 0.0, im = 0.0;
-        if (ei && fj) {
-          const int sc = (ei - 2048) + (fj - 2048) - 14;
-          re = ldexp(acc64[q], sc);
-          im = ldexp(acc64[q + 1], sc);
+        for (int h = 0; h < 2; ++h) {
+          const int64_t i = i0 + wm * 32 + mi * 16 + g + 8 * h;
+          const int64_t j = jc0 + wn * 8 + ni * 4 + tg;
+          if (i >= p.m || j >= p.n) continue;
+          if (p.lowerC && i < j) continue;
+          const int q = (mi * 2 + ni) * 4 + 2 * h;
+          const int ei = z.ea[i], fj = z.fb[j];
+          double re = 0.0, im = 0.0;
+          if (ei && fj) {
+            const int sc = (ei - 2048) + (fj - 2048) - 14;
+            re = ldexp(acc64[q], sc);
+            im = ldexp(acc64[q + 1], sc);
+          }
+          cplx v = cmul(p.alpha, mkc(re, im));
+          if (p.epi == EPI_XY) {
+            const cplx v1 = p.P[i + j * p.ldp];
+            const double s1 = p.c1[j], s2 = p.c2[j];
+            const cplx x1 = cscale(v1, 0.5 * s1), x2 = cscale(v, 0.5 * s2);
+            p.C[i + j * p.ldc] = cadd(x1, x2);
+            p.Y[i + j * p.ldy] = csub(x2, x1);
+          } else {
+            if (use_beta) v = cadd(v, cmul(p.beta, p.C[i + j * p.ldc]));
+            p.C[i + j * p.ldc] = v;
+          }
         }
-        cplx v = cmul(p.alpha, mkc(re, im));
-        if (p.epi == EPI_XY) {
-          const cplx v1 = p.P[i + j * p.ldp];
-          const double s1 = p.c1[j], s2 = p.c2[j];
-          const cplx x1 = cscale(v1, 0.5 * s1), x2 = cscale(v, 0.5 * s2);
-          p.C[i + j * p.ldc] = cadd(x1, x2);
-          p.Y[i + j * p.ldy] = csub(x2, x1);
-        } else {
-          if (use_beta) v = cadd(v, cmul(p.beta, p.C[i + j * p.ldc]));
-          p.C[i + j * p.ldc] = v;
-        }
-      }
+  } else {
+    const bool use_beta = p.beta != 0.0;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int64_t i = i0 + wm * 32 + mi * 16 + g + 8 * h;
+            const int64_t j = jc0 + wn * 16 + ni * 8 + 2 * tg + e;
+            if (i >= p.m || j >= p.n) continue;
+            if (p.lowerC && i < j) continue;
+            const int q = (mi * 2 + ni) * 4 + 2 * h + e;
+            const int ei = z.ea[i], fj = z.fb[j];
+            double v = 0.0;
+            if (ei && fj) v = ldexp(acc64[q], (ei - 2048) + (fj - 2048) - 14);
+            v *= p.alpha;
+            if (use_beta) v += p.beta * p.C[i + j * p.ldc];
+            p.C[i + j * p.ldc] = v;
+          }
+  }
+}
+
+// ---- real operands -------------------------------------------------------------
+__device__ __forceinline__ bool op_elem_d(const double* X, int64_t ldx, int op, int tri, int64_t r, int64_t c,
+                                          int64_t R, int64_t C, double* out) {
+  if (r >= R || c >= C) return false;
+  if (tri == TRI_LO && c > r) return false;
+  if (tri == TRI_UP && c < r) return false;
+  *out = (op == OPN) ? X[r + c * ldx] : X[c + r * ldx];
+  return true;
+}
+
+// exponents of rows (rowsx = 1) of op(A) or of columns (rowsx = 0) of op(B)
+__global__ void oz_exp_d_kernel(int64_t R, int64_t C, const double* X, int64_t ldx, int op, int tri, int rowsx,
+                                int* ex) {
+  __shared__ double mx[32][33];
+  const int64_t b0 = (int64_t)blockIdx.y * 32, b1 = (int64_t)blockIdx.x * 32;  // (row block, col block)
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    int64_t r, c;
+    if (op == OPN) r = b0 + tx, c = b1 + q;
+    else r = b0 + q, c = b1 + tx;
+    double v = 0.0, a = 0.0;
+    if (op_elem_d(X, ldx, op, tri, r, c, R, C, &v)) a = fabs(v);
+    const int lr = (int)(r - b0), lc = (int)(c - b1);
+    if (rowsx) mx[lr][lc] = a; else mx[lc][lr] = a;
+  }
+  __syncthreads();
+  if (ty == 0) {
+    double a = 0.0;
+    for (int q = 0; q < 32; ++q) a = fmax(a, mx[tx][q]);
+    const int64_t idx = (rowsx ? b0 : b1) + tx;
+    if (a > 0.0 && idx < (rowsx ? R : C)) {
+      int e;
+      frexp(a, &e);
+      atomicMax(ex + idx, 2048 + e);
+    }
+  }
+}
+
+// slices: rows of op(A) (trans = 0) or columns of op(B) (trans = 1) become the
+// slice rows; Xs[t][rows_p][Kp] bf16, every padded entry written
+template <int S>
+__global__ void oz_split_d_kernel(int64_t R, int64_t C, const double* X, int64_t ldx, int op, int tri, int trans,
+                                  const int* ex, int64_t Rp, int64_t Kp, uint16_t* Xs) {
+  __shared__ double tile[32][33];  // tile[slice row][k]
+  const int64_t b0 = (int64_t)blockIdx.y * 32, b1 = (int64_t)blockIdx.x * 32;  // slice-row block, k block
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    // logical element: trans = 0 -> (row b0+., k b1+.) of op(X); trans = 1 -> (k b1+., col b0+.)
+    int64_t r, c;
+    const bool contig_first = (op == OPN);  // stored contiguous along the logical row index
+    int sr, sk;
+    if (trans == 0) {
+      if (contig_first) r = b0 + tx, c = b1 + q, sr = tx, sk = q;
+      else r = b0 + q, c = b1 + tx, sr = q, sk = tx;
+    } else {
+      if (contig_first) r = b1 + tx, c = b0 + q, sr = q, sk = tx;
+      else r = b1 + q, c = b0 + tx, sr = tx, sk = q;
+    }
+    double v = 0.0;
+    op_elem_d(X, ldx, op, tri, r, c, R, C, &v);
+    tile[sr][sk] = v;
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t rr = b0 + q, kk = b1 + tx;
+    if (rr >= Rp || kk >= Kp) continue;
+    const int64_t nrows = trans ? C : R;
+    const int eb = (rr < nrows) ? ex[rr] : 0;
+    float sl[S];
+    split_value(tile[q][tx], eb ? eb - 2048 : 0, S, sl);
+    for (int t = 0; t < S; ++t) Xs[((int64_t)t * Rp + rr) * Kp + kk] = bf16_bits_exact(sl[t]);
+  }
 }
 
 }  // namespace
@@ -408,16 +512,16 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p) {
                                                                                            p.opB, p.triB, fb, Np, Kp, Bs);
   bse_count_launch(4);
   BSE_LAUNCH_CHECK();
-  OzArgs z;
+  OzArgs<cplx> z;
   z.p = p, z.As = As, z.Bs = Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np, z.Kp = Kp;
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   static bool attr = false;
   if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(oz_mma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BSE_CUDA(cudaFuncSetAttribute(oz_mma_kernel<S, cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
   dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
-  oz_mma_kernel<S><<<grid, 256, smem, s>>>(z);
+  oz_mma_kernel<S, cplx><<<grid, 256, smem, s>>>(z);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;
@@ -430,4 +534,54 @@ bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p) {
     return BSE_ERR_ARG;
   }
   return oz_run<8>(s, p);
+}
+
+template <int S>
+static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p) {
+  const int64_t Mp = (p.m + OZ_BM - 1) / OZ_BM * OZ_BM;
+  const int64_t Np = (p.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+  const int64_t Kp = (p.k + OZ_BK - 1) / OZ_BK * OZ_BK;
+  const size_t need = (size_t)S * 2 * (size_t)Kp * (size_t)(Mp + Np) + (size_t)(Mp + Np) * 4 + 1024;
+  if (!g_oz.ptr || g_oz.bytes < need) {
+    bse_internal_set_error("tensor-core GEMM workspace too small");
+    return BSE_ERR_NOMEM;
+  }
+  char* base = (char*)g_oz.ptr;
+  uint16_t* As = (uint16_t*)base;
+  uint16_t* Bs = (uint16_t*)(base + (size_t)S * Mp * Kp * 2);
+  int* ea = (int*)(base + (size_t)S * (Mp + Np) * Kp * 2);
+  int* fb = ea + Mp;
+  BSE_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (Mp + Np), s));
+  dim3 tb(32, 8);
+  oz_exp_d_kernel<<<dim3(ceil_div_u(p.k, 32), ceil_div_u(p.m, 32)), tb, 0, s>>>(p.m, p.k, p.A, p.lda, p.opA, p.triA, 1, ea);
+  oz_exp_d_kernel<<<dim3(ceil_div_u(p.n, 32), ceil_div_u(p.k, 32)), tb, 0, s>>>(p.k, p.n, p.B, p.ldb, p.opB, p.triB, 0, fb);
+  oz_split_d_kernel<S><<<dim3(ceil_div_u(Kp, 32), ceil_div_u(Mp, 32)), tb, 0, s>>>(p.m, p.k, p.A, p.lda, p.opA,
+                                                                                    p.triA, 0, ea, Mp, Kp, As);
+  oz_split_d_kernel<S><<<dim3(ceil_div_u(Kp, 32), ceil_div_u(Np, 32)), tb, 0, s>>>(p.k, p.n, p.B, p.ldb, p.opB,
+                                                                                    p.triB, 1, fb, Np, Kp, Bs);
+  bse_count_launch(4);
+  BSE_LAUNCH_CHECK();
+  OzArgs<double> z;
+  z.p = p, z.As = (const uint32_t*)As, z.Bs = (const uint32_t*)Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np,
+  z.Kp = Kp;
+  const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
+  static bool attr = false;
+  if (!attr) {
+    BSE_CUDA(cudaFuncSetAttribute(oz_mma_kernel<S, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
+  oz_mma_kernel<S, double><<<grid, 256, smem, s>>>(z);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+bse_status gemm_d_oz_raw(cudaStream_t s, const GemmParams<double>& p) {
+  if (p.m <= 0 || p.n <= 0) return BSE_OK;
+  if (p.opA == OPC || p.opB == OPC) {
+    bse_internal_set_error("tensor-core real GEMM: conjugate transpose is not meaningful");
+    return BSE_ERR_ARG;
+  }
+  return oz_run_d<8>(s, p);
 }

@@ -116,31 +116,37 @@ bse_status potrf_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, cplx* Li
 }
 
 // Solve L^H X = R in place (R: n x k, ld ldr) with L lower triangular from
-// potrf_lower and its diagonal-block inverses.  Right-looking backward
-// substitution: X_b = Linv_bb^H R_b, then R_{0:b} -= (L_{b,0:b})^H X_b.
-bse_status trsm_lower_conjtrans(cudaStream_t s, int64_t n, int64_t k, const cplx* L, int64_t ldl,
-                                const cplx* Linv, cplx* R, int64_t ldr, const int64_t* status) {
+// potrf_lower and its diagonal-block inverses.  Recursive: rows [off, off+n)
+// split at n1 (a multiple of the block size); the bottom part is solved
+// first, the top right-hand side takes one large update
+//   R1 -= (L21)^H R2,   L21 = L(off+n1 : off+n, off : off+n1),
+// then the top part is solved; a leaf (one diagonal block) is X = Linv^H R.
+static bse_status trsm_rec(cudaStream_t s, int64_t off, int64_t n, int64_t k, const cplx* L, int64_t ldl,
+                           const cplx* Linv, cplx* R, int64_t ldr, const int64_t* status) {
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), mone = mkc(-1.0, 0.0);
-  const int64_t nblk = (n + CHOL_NB - 1) / CHOL_NB;
-  for (int64_t b = nblk - 1; b >= 0; --b) {
-    const int64_t k0 = b * CHOL_NB;
-    const int64_t bs = (n - k0) < CHOL_NB ? (n - k0) : CHOL_NB;
-    const cplx* Li = Linv + b * CHOL_NB * CHOL_NB;
-    cplx* Rb = R + k0;
-    // in place: m = bs <= 64 means one CTA row; every CTA reads all bs rows of
-    // its columns before writing them.
-    GemmParams<cplx> p = gemm_params<cplx>(bs, k, bs, OPC, Li, CHOL_NB, OPN, Rb, ldr, one, zero, Rb, ldr);
+  if (n <= CHOL_NB) {
+    const cplx* Li = Linv + (off / CHOL_NB) * CHOL_NB * CHOL_NB;
+    cplx* Rb = R + off;
+    // in place: m = n <= 64 means one CTA row (DFMA engine) or a split that
+    // reads all of Rb before the product writes it (tensor-core engine)
+    GemmParams<cplx> p = gemm_params<cplx>(n, k, n, OPC, Li, CHOL_NB, OPN, Rb, ldr, one, zero, Rb, ldr);
     p.triA = TRI_UP;
     p.status = status;
-    bse_status r = gemm_z(s, p);
-    if (r) return r;
-    if (k0 > 0) {
-      GemmParams<cplx> q =
-          gemm_params<cplx>(k0, k, bs, OPC, L + k0, ldl, OPN, Rb, ldr, mone, one, R, ldr);
-      q.status = status;
-      r = gemm_z(s, q);
-      if (r) return r;
-    }
+    return gemm_z(s, p);
   }
-  return BSE_OK;
+  const int64_t half = (n + 1) / 2;
+  const int64_t n1 = (half + CHOL_NB - 1) / CHOL_NB * CHOL_NB, n2 = n - n1;
+  bse_status r = trsm_rec(s, off + n1, n2, k, L, ldl, Linv, R, ldr, status);
+  if (r) return r;
+  GemmParams<cplx> q = gemm_params<cplx>(n1, k, n2, OPC, L + IDX2(off + n1, off, ldl), ldl, OPN, R + off + n1, ldr,
+                                         mone, one, R + off, ldr);
+  q.status = status;
+  if ((r = gemm_z(s, q))) return r;
+  return trsm_rec(s, off, n1, k, L, ldl, Linv, R, ldr, status);
+}
+
+bse_status trsm_lower_conjtrans(cudaStream_t s, int64_t n, int64_t k, const cplx* L, int64_t ldl,
+                                const cplx* Linv, cplx* R, int64_t ldr, const int64_t* status) {
+  if (n <= 0 || k <= 0) return BSE_OK;
+  return trsm_rec(s, 0, n, k, L, ldl, Linv, R, ldr, status);
 }

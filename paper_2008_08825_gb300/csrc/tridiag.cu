@@ -109,10 +109,28 @@ __device__ __forceinline__ int find_block(const int* bstart, int nb, int64_t s, 
   return lo;
 }
 
+// Sturm counts of an unreduced T at TRI_GRID - 1 equally spaced interior
+// points of the spectrum's enclosing interval: every eigenvalue's bisection
+// then starts from the grid cell that contains it (log2(TRI_GRID) halvings
+// saved), with the same invariant count(lo) <= t < count(hi).
+constexpr int TRI_GRID = 8192;
+
+__global__ void tri_grid_kernel(int64_t N, const double* __restrict__ a, const double* __restrict__ e2,
+                                const int* __restrict__ iprm, const double* __restrict__ prm, int* __restrict__ cnt,
+                                const int64_t* status) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= TRI_GRID - 1) return;
+  if (*(volatile const int64_t*)status) return;
+  if (iprm[0] != 1) return;  // split matrices bisect from the full interval
+  const double lo = prm[3], hi = prm[4];
+  const double x = lo + (hi - lo) * ((double)(g + 1) / (double)TRI_GRID);
+  cnt[g] = sturm_count(a, e2, 0, (int)N, x, prm[0]);
+}
+
 __global__ void tri_bisect_kernel(int64_t total, const double* __restrict__ a, const double* __restrict__ e2,
                                   const int* __restrict__ bstart, const int* __restrict__ iprm,
                                   const double* __restrict__ prm, int mode, double* __restrict__ lam,
-                                  int* __restrict__ blk, const int64_t* status) {
+                                  int* __restrict__ blk, const int* __restrict__ cnt, const int64_t* status) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= total) return;
   if (*(volatile const int64_t*)status) return;
@@ -123,6 +141,19 @@ __global__ void tri_bisect_kernel(int64_t total, const double* __restrict__ a, c
   const int t = mode == 0 ? (int)(s - b0) : m / 2 + (int)(s - b0 / 2);
   const double pivmin = prm[0];
   double lo = prm[3], hi = prm[4];
+  if (nb == 1) {
+    // first grid point with count > t: eigenvalue t lies in (x_{g}, x_{g+1}]
+    int l = 0, h = TRI_GRID - 1;  // search over cnt[0 .. TRI_GRID-2]; h = "none"
+    while (l < h) {
+      const int mid = (l + h) >> 1;
+      if (cnt[mid] > t) h = mid; else l = mid + 1;
+    }
+    const double w = (hi - lo) / (double)TRI_GRID;
+    const double glo = l > 0 ? lo + w * (double)l : lo;
+    const double ghi = l < TRI_GRID - 1 ? lo + w * (double)(l + 1) : hi;
+    lo = glo;
+    hi = ghi;
+  }
   for (int it = 0; it < 256; ++it) {
     const double mid = 0.5 * (lo + hi);
     const double w = hi - lo;
@@ -277,8 +308,13 @@ bse_status tridiag_eig(cudaStream_t s, int64_t N, const double* a, const double*
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   prof_launch_begin(s);
+  tri_grid_kernel<<<ceil_div_u(TRI_GRID, 128), 128, 0, s>>>(N, w.a, w.e2, w.iprm, w.prm, w.grid, status);
+  prof_launch_end(s, "tri_grid_kernel");
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  prof_launch_begin(s);
   tri_bisect_kernel<<<ceil_div_u(total, 64), 64, 0, s>>>(total, w.a, w.e2, w.bstart, w.iprm, w.prm, mode, w.lam,
-                                                         w.blk, status);
+                                                         w.blk, w.grid, status);
   prof_launch_end(s, "tri_bisect_kernel");
   bse_count_launch();
   BSE_LAUNCH_CHECK();
@@ -294,3 +330,5 @@ bse_status tridiag_eig(cudaStream_t s, int64_t N, const double* a, const double*
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
+
+int tri_grid_points() { return TRI_GRID; }
