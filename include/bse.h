@@ -170,7 +170,7 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
                           bse_info* info, void* stream);
 
 /*
- * Batched Cholesky method (Alg. 2 for each instance): `count` independent
+ * Batched solves (Alg. 2 or Alg. 3 for each instance): `count` independent
  * problems of sizes n[i] (1 <= n[i] <= 1024), the k lowest eigenpairs of each
  * (k_i = min(k, n[i])), in ONE persistent kernel launch: each CTA takes the
  * next instance from a queue ordered by decreasing n and solves it alone.
@@ -183,7 +183,7 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
  * status   host array of count int64 (may be NULL): 0 or the instance's
  *          bse_status code.  The return value is BSE_OK when every instance
  *          succeeded, else the first failing instance's code.
- * method   BSE_METHOD_CHOL (BSE_METHOD_SVD returns BSE_ERR_NOT_IMPLEMENTED);
+ * method   BSE_METHOD_CHOL or BSE_METHOD_SVD;
  * prec     BSE_PREC_FP64.
  */
 bse_status bse_solve_batched(bse_handle h, int64_t count, const int64_t* n, const double* const* A,

@@ -303,14 +303,16 @@ class Omega(torch.autograd.Function):
 
 class Batch:
     """Device buffers and pointer tables of a batched solve (the k lowest pairs
-    of many instances, Alg. 2 each, one persistent launch).
+    of many instances, Alg. 2 or Alg. 3 each, one persistent launch).
 
-    instances: list of (A, B) complex128 CUDA tensors (n_i x n_i, n_i <= 1024).
+    instances: list of (A, B) complex128 CUDA tensors (n_i x n_i, n_i <= 1024);
+    method: "chol" (Alg. 2) or "svd" (Alg. 3).
     """
 
-    def __init__(self, instances, k: int = 32):
+    def __init__(self, instances, k: int = 32, method: str = "chol"):
         self.count = len(instances)
         self.k = int(k)
+        self.method = method
         dev = instances[0][0].device if instances else torch.device("cuda")
         self.n = [int(A.shape[0]) for A, _ in instances]
         self.A = [_colmajor(A) for A, _ in instances]
@@ -332,7 +334,7 @@ class Batch:
         self._Y = arr(ctypes.c_void_p, [t.data_ptr() for t in self.Yt])
 
     def _args(self):
-        return (self.count, self._n, self._A, self._B, self.k, 0, 0, self._om, self._X, self._Y)
+        return (self.count, self._n, self._A, self._B, self.k, METHODS[self.method], 0, self._om, self._X, self._Y)
 
     def run(self, handle: Handle | None = None, stream=None):
         """Synchronous solve; raises on the first failing instance."""

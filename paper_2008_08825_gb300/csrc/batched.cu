@@ -12,6 +12,14 @@
 //   time (a warp per column, no barriers); P = L^{-H} V_M by column-wise
 //   substitution; X, Y from P and L V_M through the tile routine's fused
 //   epilogue (Alg. 2 steps 4-6).
+// The SVD method (Alg. 3 per instance, batched_svd_kernel) runs the same way:
+//   two blocked Choleskys L1 L1^H = A + B, L2 L2^H = A - B; G = L1^H L2
+//   (tile routine); unblocked Householder bidiagonalisation G = Q B P^H (a
+//   warp per column for the left reflectors, a row matvec plus a warp per
+//   column for the right ones); bisection on the Golub-Kahan form of B for
+//   the k smallest singular values; twisted-factorisation vectors split into
+//   U_B, V_B; one Newton-Schulz step on each; U = Q U_B, V = P V_B one
+//   reflector at a time; X, Y from L1 U and L2 V through the fused epilogue.
 // A whole instance stays on one SM, so nothing synchronises across CTAs;
 // the only global atomic is the queue counter.
 #include <float.h>
@@ -99,7 +107,8 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
 __device__ __forceinline__ double cta_min(double v, double* red) { return -cta_max(-v, red); }
 
 // ---- Cholesky of the lower triangle of L (n x n, ld n), block CNB ----------
-__device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx* S, cplx* Iv, int* flag) {
+__device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx* S, cplx* Iv, int* flag,
+                          int64_t err_code) {
   const int tid = threadIdx.x;
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), mone = mkc(-1.0, 0.0);
   for (int64_t k0 = 0; k0 < n; k0 += CNB) {
@@ -116,7 +125,7 @@ __device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx*
         const double dd = S[j + j * CLD].x;
         if (!(dd > 0.0)) {
           *flag = 1;
-          status[0] = BSE_ERR_NOT_PD_AMINUSB;
+          status[0] = err_code;
           status[1] = k0 + j + 1;
         } else {
           S[j + j * CLD] = mkc(sqrt(dd), 0.0);
@@ -286,7 +295,7 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
   }
   __threadfence_block();
   __syncthreads();
-  if (!cta_potrf(n, w.L, w.Linv, st, S, Iv, flag)) return;
+  if (!cta_potrf(n, w.L, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_AMINUSB)) return;
   // W = M1 L ; M = L^H W (lower) into M1
   GemmParams<cplx> p1 = gemm_params<cplx>(n, n, n, OPN, w.M1, n, OPN, w.L, n, one, zero, w.W, n);
   p1.triB = TRI_LO;
@@ -451,6 +460,336 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
   gemm_cta<cplx, 8>(p3);
 }
 
+// ---- Alg. 3 for one instance --------------------------------------------------
+// Workspace: L1, L2, G, Vr (n x n each), tauq, taup (n), d, e, off, e2 (2n),
+// Z, sc (2n x k), UB, VB (n x k real), Uc, Vc, T1 (n x k complex), E, c (k).
+struct SvdWs {
+  cplx *L1, *L2, *G, *Vr, *Linv, *tauq, *taup, *Uc, *Vc, *T1;
+  double *d, *e, *off, *e2, *Z, *sc, *UB, *VB, *E, *c1;
+};
+
+__host__ __device__ inline size_t carve_svd_inst(char* base, int64_t n, int64_t k, SvdWs* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = align256(off);
+    char* p = base ? base + off : nullptr;
+    off += bytes > 0 ? bytes : 1;
+    return p;
+  };
+  const size_t nn = (size_t)n * n, nk = (size_t)n * k;
+  SvdWs t;
+  t.L1 = (cplx*)take(nn * 16);
+  t.L2 = (cplx*)take(nn * 16);
+  t.G = (cplx*)take(nn * 16);
+  t.Vr = (cplx*)take(nn * 16);
+  t.Linv = (cplx*)take(CNB * CNB * 16);
+  t.tauq = (cplx*)take(n * 16);
+  t.taup = (cplx*)take(n * 16);
+  t.Uc = (cplx*)take(nk * 16);
+  t.Vc = (cplx*)take(nk * 16);
+  t.T1 = (cplx*)take(nk * 16);
+  t.d = (double*)take(n * 8);
+  t.e = (double*)take(n * 8);
+  t.off = (double*)take(2 * n * 8);
+  t.e2 = (double*)take(2 * n * 8);
+  t.Z = (double*)take(2 * nk * 8);
+  t.sc = (double*)take(2 * nk * 8);
+  t.UB = (double*)take(nk * 8);
+  t.VB = (double*)take(nk * 8);
+  t.E = (double*)take((size_t)k * k * 8);
+  t.c1 = (double*)take(k * 8);
+  if (w) *w = t;
+  return align256(off);
+}
+
+size_t batched_svd_inst_bytes(int64_t n, int64_t k) { return carve_svd_inst(nullptr, n, k, nullptr); }
+
+// Householder reflector of x = (alpha, rest) with ||rest||^2 = xn2: H^H x = beta e_1
+__device__ __forceinline__ void house_params(cplx alpha, double xn2, cplx* tau, cplx* scal, double* beta) {
+  if (xn2 == 0.0 && alpha.y == 0.0) {
+    *tau = mkc(0.0, 0.0);
+    *beta = alpha.x;
+    *scal = mkc(0.0, 0.0);
+  } else {
+    const double nr = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+    const double b = (alpha.x >= 0.0) ? -nr : nr;
+    *beta = b;
+    *tau = mkc((b - alpha.x) / b, -alpha.y / b);
+    *scal = cdiv(mkc(1.0, 0.0), mkc(alpha.x - b, alpha.y));
+  }
+}
+
+// unblocked bidiagonalisation of G (n x n, ld n): left reflector u_i kept in
+// G(i:, i) (unit first entry), right reflector v_i in Vr(i+1:, i)
+__device__ void cta_gebrd(int64_t n, cplx* G, cplx* Vr, cplx* tauq, cplx* taup, double* d, double* e, cplx* ts,
+                          double* red) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ cplx h_tau, h_scal;
+  __shared__ double h_beta;
+  for (int64_t i = 0; i < n; ++i) {
+    // left reflector on G(i:, i)
+    double nrm = 0.0;
+    for (int64_t r = i + 1 + tid; r < n; r += BT) nrm += cabs2(G[IDX2(r, i, n)]);
+    nrm = cta_sum(nrm, red);
+    if (tid == 0) {
+      cplx t, sc;
+      double b;
+      house_params(G[IDX2(i, i, n)], nrm, &t, &sc, &b);
+      h_tau = t, h_scal = sc, h_beta = b;
+      tauq[i] = t;
+      d[i] = b;
+    }
+    __syncthreads();
+    for (int64_t r = i + tid; r < n; r += BT)
+      G[IDX2(r, i, n)] = (r == i) ? mkc(1.0, 0.0) : cmul(G[IDX2(r, i, n)], h_scal);
+    __syncthreads();
+    // G(i:, c) -= conj(tau) u (u^H G(i:, c)), c > i: warp per column
+    const cplx ctau = cconj(h_tau);
+    for (int64_t c = i + 1 + warp; c < n; c += BT / 32) {
+      cplx sdot = mkc(0.0, 0.0);
+      for (int64_t r = i + lane; r < n; r += 32) cfma_cj(sdot, G[IDX2(r, i, n)], G[IDX2(r, c, n)]);
+      for (int o = 16; o > 0; o >>= 1) {
+        sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o);
+        sdot.y += __shfl_xor_sync(0xffffffffu, sdot.y, o);
+      }
+      const cplx f = cmul(ctau, sdot);
+      for (int64_t r = i + lane; r < n; r += 32) G[IDX2(r, c, n)] = csub(G[IDX2(r, c, n)], cmul(G[IDX2(r, i, n)], f));
+    }
+    __syncthreads();
+    if (i + 1 >= n) break;
+    // right reflector from x = conj(G(i, i+1:))
+    nrm = 0.0;
+    for (int64_t c = i + 2 + tid; c < n; c += BT) nrm += cabs2(G[IDX2(i, c, n)]);
+    nrm = cta_sum(nrm, red);
+    if (tid == 0) {
+      cplx t, sc;
+      double b;
+      house_params(cconj(G[IDX2(i, i + 1, n)]), nrm, &t, &sc, &b);
+      h_tau = t, h_scal = sc, h_beta = b;
+      taup[i] = t;
+      e[i] = b;
+    }
+    __syncthreads();
+    for (int64_t c = i + 1 + tid; c < n; c += BT)
+      Vr[IDX2(c, i, n)] = (c == i + 1) ? mkc(1.0, 0.0) : cmul(cconj(G[IDX2(i, c, n)]), h_scal);
+    __syncthreads();
+    // G(i+1:, i+1:) <- G - tau (G v) v^H: t = G v by rows, then warp per column
+    for (int64_t r = i + 1 + tid; r < n; r += BT) {
+      cplx acc = mkc(0.0, 0.0);
+      for (int64_t c = i + 1; c < n; ++c) cfma(acc, G[IDX2(r, c, n)], Vr[IDX2(c, i, n)]);
+      ts[r - i - 1] = cmul(h_tau, acc);
+    }
+    __syncthreads();
+    for (int64_t c = i + 1 + warp; c < n; c += BT / 32) {
+      const cplx vc = cconj(Vr[IDX2(c, i, n)]);
+      for (int64_t r = i + 1 + lane; r < n; r += 32) G[IDX2(r, c, n)] = csub(G[IDX2(r, c, n)], cmul(ts[r - i - 1], vc));
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cplx* S, cplx* Iv, int* flag) {
+  const int64_t n = D.n, k = D.k;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  SvdWs w;
+  carve_svd_inst(D.ws, n, k, &w);
+  int64_t* st = D.status;
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  for (int64_t q = tid; q < n * n; q += BT) {
+    const int64_t i = q % n, j = q / n;
+    if (i >= j) {
+      const cplx a = D.A[IDX2(i, j, n)], b = D.B[IDX2(i, j, n)];
+      w.L1[q] = (i == j) ? mkc(a.x + b.x, 0.0) : cadd(a, b);
+      w.L2[q] = (i == j) ? mkc(a.x - b.x, 0.0) : csub(a, b);
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (!cta_potrf(n, w.L1, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_APLUSB)) return;
+  if (!cta_potrf(n, w.L2, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_AMINUSB)) return;
+  // G = L1^H L2
+  GemmParams<cplx> pg = gemm_params<cplx>(n, n, n, OPC, w.L1, n, OPN, w.L2, n, one, zero, w.G, n);
+  pg.triA = TRI_UP;
+  pg.triB = TRI_LO;
+  gemm_cta<cplx, 8>(pg);
+  __threadfence_block();
+  __syncthreads();
+  cta_gebrd(n, w.G, w.Vr, w.tauq, w.taup, w.d, w.e, vs, red);
+  // Golub-Kahan tridiagonal (zero diagonal), size N = 2n
+  const int64_t N = 2 * n;
+  double tn = 0.0, em = 0.0;
+  for (int64_t i = tid; i < N - 1; i += BT) {
+    const double o = (i & 1) ? w.e[i >> 1] : w.d[i >> 1];
+    w.off[i] = o;
+    w.e2[i] = o * o;
+    tn = fmax(tn, 2.0 * fabs(o));
+    em = fmax(em, o * o);
+  }
+  tn = cta_max(tn, red);
+  em = cta_max(em, red);
+  __threadfence_block();
+  __syncthreads();
+  const double pivmin = DBL_MIN * fmax(1.0, em), g = DBL_EPSILON * fmax(tn, DBL_MIN);
+  const double lo0 = -tn - 4.0 * pivmin, hi0 = tn + 4.0 * pivmin;
+  for (int64_t t = tid; t < k; t += BT) {
+    const int tt = (int)(n + t);  // the (t+1)-th smallest positive eigenvalue of TGK
+    double a = lo0, b = hi0;
+    for (int it = 0; it < 256; ++it) {
+      const double mid = 0.5 * (a + b), wd = b - a;
+      if (wd <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)) || wd <= 4.0 * pivmin || mid == a || mid == b) break;
+      double q = -mid;
+      if (fabs(q) < pivmin) q = -pivmin;
+      int cnt = q < 0.0;
+      for (int64_t i = 1; i < N; ++i) {
+        q = -mid - w.e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0;
+      }
+      if (cnt > tt) b = mid; else a = mid;
+    }
+    const double l = 0.5 * (a + b);
+    double* zc = w.Z + t * N;
+    double* sc = w.sc + t * N;
+    double x = -l;
+    if (fabs(x) < g) x = (x < 0.0) ? -g : g;
+    zc[0] = x;
+    for (int64_t i = 1; i < N; ++i) {
+      x = -l - w.e2[i - 1] / x;
+      if (fabs(x) < g) x = (x < 0.0) ? -g : g;
+      zc[i] = x;
+    }
+    double y = -l;
+    if (fabs(y) < g) y = (y < 0.0) ? -g : g;
+    sc[N - 1] = y;
+    double best = fabs(zc[N - 1]);
+    int64_t r = N - 1;
+    for (int64_t i = N - 2; i >= 0; --i) {
+      y = -l - w.e2[i] / y;
+      if (fabs(y) < g) y = (y < 0.0) ? -g : g;
+      sc[i] = y;
+      const double gam = zc[i] + y + l;
+      if (fabs(gam) < best) best = fabs(gam), r = i;
+    }
+    double nrm2 = 1.0, z = 1.0;
+    for (int64_t i = r - 1; i >= 0; --i) {
+      z = -(w.off[i] / zc[i]) * z;
+      zc[i] = z;
+      nrm2 += z * z;
+    }
+    zc[r] = 1.0;
+    z = 1.0;
+    for (int64_t i = r; i < N - 1; ++i) {
+      z = -(w.off[i] / sc[i + 1]) * z;
+      zc[i + 1] = z;
+      nrm2 += z * z;
+    }
+    const double inv = sqrt(2.0 / nrm2);  // u, v halves get unit norm
+    for (int64_t i = 0; i < n; ++i) {
+      w.VB[i + t * n] = zc[2 * i] * inv;
+      w.UB[i + t * n] = zc[2 * i + 1] * inv;
+    }
+    if (!(l > 0.0)) {
+      st[0] = BSE_ERR_NOT_PD_APLUSB;
+      st[1] = 0;
+    }
+    D.omega[t] = l;
+    w.c1[t] = 1.0 / sqrt(l);
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (st[0]) return;
+  // Newton-Schulz on U_B and V_B (k x k Gram, plain loops)
+  for (int pass = 0; pass < 2; ++pass) {
+    double* Zm = pass == 0 ? w.UB : w.VB;
+    for (int64_t q = tid; q < k * k; q += BT) {
+      const int64_t a = q % k, b = q / k;
+      if (a < b) continue;
+      double s2 = 0.0;
+      for (int64_t i = 0; i < n; ++i) s2 = fma(Zm[i + a * n], Zm[i + b * n], s2);
+      if (a == b) s2 -= 1.0;
+      w.E[a + b * k] = s2;
+      w.E[b + a * k] = s2;
+    }
+    __threadfence_block();
+    __syncthreads();
+    for (int64_t q = tid; q < n * k; q += BT) {
+      const int64_t i = q % n, c = q / n;
+      double s2 = 0.0;
+      for (int64_t b = 0; b < k; ++b) s2 = fma(Zm[i + b * n], w.E[b + c * k], s2);
+      w.sc[q] = Zm[q] - 0.5 * s2;
+    }
+    __threadfence_block();
+    __syncthreads();
+    cplx* out = pass == 0 ? w.Uc : w.Vc;
+    for (int64_t q = tid; q < n * k; q += BT) out[q] = mkc(w.sc[q], 0.0);
+    __threadfence_block();
+    __syncthreads();
+  }
+  // back-transformations: U = H_L(0) ... H_L(n-1) U_B, V = H_R(0) ... H_R(n-2) V_B
+  for (int64_t c = warp; c < k; c += BT / 32) {
+    cplx* uc = w.Uc + c * n;
+    for (int64_t j = n - 1; j >= 0; --j) {
+      const cplx* u = w.G + IDX2(j, j, n);
+      const int64_t m = n - j;
+      cplx sdot = mkc(0.0, 0.0);
+      for (int64_t r = lane; r < m; r += 32) cfma_cj(sdot, u[r], uc[j + r]);
+      for (int o = 16; o > 0; o >>= 1) {
+        sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o);
+        sdot.y += __shfl_xor_sync(0xffffffffu, sdot.y, o);
+      }
+      const cplx f = cmul(w.tauq[j], sdot);
+      for (int64_t r = lane; r < m; r += 32) uc[j + r] = csub(uc[j + r], cmul(u[r], f));
+      __syncwarp();
+    }
+    cplx* vc = w.Vc + c * n;
+    for (int64_t j = n - 2; j >= 0; --j) {
+      const cplx* v = w.Vr + IDX2(j + 1, j, n);
+      const int64_t m = n - j - 1;
+      cplx sdot = mkc(0.0, 0.0);
+      for (int64_t r = lane; r < m; r += 32) cfma_cj(sdot, v[r], vc[j + 1 + r]);
+      for (int o = 16; o > 0; o >>= 1) {
+        sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o);
+        sdot.y += __shfl_xor_sync(0xffffffffu, sdot.y, o);
+      }
+      const cplx f = cmul(w.taup[j], sdot);
+      for (int64_t r = lane; r < m; r += 32) vc[j + 1 + r] = csub(vc[j + 1 + r], cmul(v[r], f));
+      __syncwarp();
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  // T1 = L1 U; X, Y from T1 and L2 V, c1 = c2 = omega^{-1/2}
+  GemmParams<cplx> p1 = gemm_params<cplx>(n, k, n, OPN, w.L1, n, OPN, w.Uc, n, one, zero, w.T1, n);
+  p1.triA = TRI_LO;
+  gemm_cta<cplx, 8>(p1);
+  __threadfence_block();
+  __syncthreads();
+  GemmParams<cplx> p2 = gemm_params<cplx>(n, k, n, OPN, w.L2, n, OPN, w.Vc, n, one, zero, D.X, n);
+  p2.triA = TRI_LO;
+  p2.epi = EPI_XY;
+  p2.P = w.T1, p2.ldp = n, p2.c1 = w.c1, p2.c2 = w.c1, p2.Y = D.Y, p2.ldy = n;
+  gemm_cta<cplx, 8>(p2);
+}
+
+__global__ void __launch_bounds__(BT, 1) batched_svd_kernel(const BatchDesc* __restrict__ desc, int64_t count,
+                                                            int* counter) {
+  extern __shared__ cplx dyn[];
+  cplx* vs = dyn;                    // 1024
+  cplx* S = dyn + 2048;              // CNB x CLD
+  cplx* Iv = S + CNB * CLD;          // CNB x CLD
+  __shared__ double red[BT / 32];
+  __shared__ int next, flag;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = next;
+    __syncthreads();
+    if (idx >= count) break;
+    solve_instance_svd(desc[idx], vs, red, S, Iv, &flag);
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(const BatchDesc* __restrict__ desc, int64_t count,
                                                              int* counter) {
   extern __shared__ cplx dyn[];
@@ -473,15 +812,19 @@ __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(const BatchDesc* __
 
 size_t batched_smem_bytes() { return sizeof(cplx) * (2048 + 2 * CNB * CLD); }
 
-bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid) {
+bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid, int method) {
   static bool attr = false;
   const size_t smem = batched_smem_bytes();
   if (!attr) {
     BSE_CUDA(cudaFuncSetAttribute(batched_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BSE_CUDA(cudaFuncSetAttribute(batched_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   BSE_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
-  batched_chol_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
+  if (method == BSE_METHOD_SVD)
+    batched_svd_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
+  else
+    batched_chol_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;

@@ -474,8 +474,7 @@ static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* 
                                   cudaStream_t s) {
   if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
   if (count < 0 || k < 1) return bse_internal_set_error("count < 0 or k < 1"), BSE_ERR_ARG;
-  if (method == BSE_METHOD_SVD) return bse_internal_set_error("batched SVD method is not available in this build"), BSE_ERR_NOT_IMPLEMENTED;
-  if (method != BSE_METHOD_CHOL) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
+  if (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
   if (prec != BSE_PREC_FP64) return bse_internal_set_error("batched solves are FP64 only"), BSE_ERR_NOT_IMPLEMENTED;
   if (count == 0) return BSE_OK;
   if (!n || !A || !B || !omega || !X || !Y) return bse_internal_set_error("NULL array"), BSE_ERR_ARG;
@@ -492,7 +491,8 @@ static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* 
   for (int64_t q = 0; q < count; ++q) {
     const int64_t i = order[q];
     offs[q] = ws_total;
-    ws_total += batched_inst_bytes(n[i], k < n[i] ? k : n[i]);
+    const int64_t ki = k < n[i] ? k : n[i];
+    ws_total += method == BSE_METHOD_SVD ? batched_svd_inst_bytes(n[i], ki) : batched_inst_bytes(n[i], ki);
   }
   const size_t desc_bytes = (batched_desc_bytes() * count + 255) & ~(size_t)255;
   const size_t stat_bytes = ((size_t)16 * count + 255) & ~(size_t)255;
@@ -529,7 +529,7 @@ static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* 
   BSE_CUDA(cudaMemcpyAsync(ddesc, h->bdesc_host, batched_desc_bytes() * count, cudaMemcpyHostToDevice, s));
   BSE_CUDA(cudaMemsetAsync(dstat, 0, 16 * count, s));
   const int grid = (int)std::min<int64_t>(count, (int64_t)h->sms * h->batch_cps);
-  TRY(batched_chol_launch(s, ddesc, count, counter, grid));
+  TRY(batched_chol_launch(s, ddesc, count, counter, grid, method));
   if (dstatus_out) *dstatus_out = dstat;
   return BSE_OK;
 }
@@ -649,8 +649,7 @@ bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t
 bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, int64_t lda, const double* B,
                           int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx,
                           double* Y, int64_t ldy, bse_info* info, void* stream) {
-  if (method == BSE_METHOD_SVD) return bse_internal_set_error("batched SVD method is not available in this build"), BSE_ERR_NOT_IMPLEMENTED;
-  if (method != BSE_METHOD_CHOL) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
+  if (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
   bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
   if (r != BSE_OK || n == 0) return r;
   cudaStream_t s = (cudaStream_t)stream;

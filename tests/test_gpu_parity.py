@@ -228,10 +228,11 @@ def _batch_instances(idx, dev, sizes=None):
     return out, host
 
 
-def test_batched_persistent_kernel_vs_oracle(dev):
+@pytest.mark.parametrize("method", ["chol", "svd"])
+def test_batched_persistent_kernel_vs_oracle(dev, method):
     """One persistent launch over uneven instances (the largest sizes of the
     512-instance workload plus small and odd ones): lowest 32 pairs of each
-    against the oracle."""
+    against the oracle, Alg. 2 or Alg. 3 in every instance."""
     sizes = inputs.batched_sizes()
     order = np.argsort(-sizes)
     idx = list(order[:3]) + [int(np.argmin(sizes))] + [0, 1, 2, 7, 11]
@@ -240,7 +241,7 @@ def test_batched_persistent_kernel_vs_oracle(dev):
     for A, B in extra:
         host.append((A, B))
         inst.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
-    bt = bse.Batch(inst, k=32).run()
+    bt = bse.Batch(inst, k=32, method=method).run()
     assert all(s == 0 for s in bt.status)
     for (A, B), (om, X, Y) in zip(host, bt.results()):
         om, X, Y = om.cpu().numpy(), X.cpu().numpy(), Y.cpu().numpy()
