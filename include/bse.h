@@ -48,7 +48,8 @@ typedef enum {
   BSE_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired */
   BSE_ERR_CUDA = 7,             /* a CUDA runtime call failed (see bse_last_error) */
   BSE_ERR_NOMEM = 8,            /* workspace allocation failed */
-  BSE_ERR_NOT_IMPLEMENTED = 9   /* option not supported by this build */
+  BSE_ERR_NOT_IMPLEMENTED = 9,  /* option not supported by this build */
+  BSE_ERR_TOO_LARGE = 10        /* bse_solve_chol_noalloc: n above BSE_NOALLOC_MAX_N */
 } bse_status;
 
 typedef enum { BSE_PREC_FP64 = 0, BSE_PREC_MIXED = 1 } bse_precision;
@@ -237,6 +238,38 @@ bse_status bse_profile_read(bse_handle h, bse_profile_data* out);
 /* Level-2 per-kernel summary, one "name launches total_ms" line per kernel,
  * written NUL-terminated into buf (truncated to len); returns the full length. */
 int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
+
+/*
+ * Allocation-free Cholesky solve of ONE small problem.  The paper has no
+ * counterpart: this entry point serves callers that cannot allocate device
+ * memory (device memory wholly held by another allocator's pool; latency-
+ * critical loops where cudaMalloc/cudaFree would lock or synchronise the
+ * device; services that must not meet out-of-memory after start-up).  It
+ * computes what bse_solve_chol computes with il = 1, iu = k (Alg. 2, the
+ * lowest k pairs), with one thread block on one SM, and allocates nothing:
+ * no device or pinned memory, no handle, no host heap.  Its workspace is a
+ * fixed __device__ array of BSE_NOALLOC_SCRATCH_BYTES, created with the
+ * library's module on each device that uses it.
+ * n        1 <= n <= BSE_NOALLOC_MAX_N; larger n returns BSE_ERR_TOO_LARGE
+ *          without launching anything; n == 0 or k == 0 returns BSE_OK.
+ * k        0 <= k <= n.
+ * A, B     device, n x n Hermitian, leading dimension n (packed), lower
+ *          triangle read.
+ * omega    device, k doubles (ascending).
+ * X, Y     device, n x k, leading dimension n.
+ * info     host, may be NULL: info->info = failing 1-based column for the
+ *          not-positive-definite codes, else 0.
+ * stream   work is enqueued on it, then the stream is synchronised.
+ * Set-up: the first call with a device current looks up the scratch address
+ * for that device; make that first call before any stream capture on it.
+ * Calls that overlap on one device share the scratch and race: serialise
+ * them.  This entry point reports through its return code only; it does not
+ * update bse_last_error().
+ */
+#define BSE_NOALLOC_MAX_N 256
+#define BSE_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
+bse_status bse_solve_chol_noalloc(int64_t n, int64_t k, const double* A, const double* B, double* omega, double* X,
+                                  double* Y, bse_info* info, void* stream);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,9 @@ STATUS_NAMES = {
     7: "BSE_ERR_CUDA",
     8: "BSE_ERR_NOMEM",
     9: "BSE_ERR_NOT_IMPLEMENTED",
+    10: "BSE_ERR_TOO_LARGE",
 }
+NOALLOC_MAX_N = 256
 METHODS = {"chol": 0, "svd": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
@@ -81,6 +83,8 @@ def _bind(lib):
     for f in (lib.bse_solve_batched, lib.bse_solve_batched_async):
         f.argtypes = [_P, _I64, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
         f.restype = ctypes.c_int
+    lib.bse_solve_chol_noalloc.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P]
+    lib.bse_solve_chol_noalloc.restype = ctypes.c_int
     lib.bse_set_option.argtypes = [_P, ctypes.c_int, _I64]
     lib.bse_set_option.restype = ctypes.c_int
     lib.bse_profile_enable.argtypes = [_P, ctypes.c_int]
@@ -225,6 +229,36 @@ def solve(A: torch.Tensor, B: torch.Tensor, method: str = "chol", precision: str
         return omega, None, None
     return omega, Xt.mT, Yt.mT
 
+
+
+def solve_noalloc(A: torch.Tensor, B: torch.Tensor, k: int, omega: torch.Tensor, Xt: torch.Tensor, Yt: torch.Tensor,
+                  stream=None):
+    '''The k lowest pairs of one small problem (n <= NOALLOC_MAX_N) through
+    bse_solve_chol_noalloc, which allocates nothing (for callers that cannot
+    allocate: memory held by another allocator's pool, latency-critical loops).
+    Every buffer is the caller's and is used in place: A, B complex128
+    column-major (A.mT contiguous, n x n), omega (k,) float64, Xt, Yt (k, n)
+    complex128 contiguous (Xt.mT is X).  This wrapper allocates nothing on the
+    device either.  Raises BseError on a nonzero status.
+    '''
+    n = int(A.shape[0])
+    for T in (A, B):
+        if T.dtype != torch.complex128 or not T.is_cuda or not _is_colmajor(T):
+            raise TypeError("bse: A and B must be column-major complex128 device tensors")
+    if omega.dtype != torch.float64 or omega.numel() < k or not omega.is_contiguous():
+        raise TypeError("bse: omega must be a contiguous float64 tensor of k elements")
+    for T in (Xt, Yt):
+        if T.dtype != torch.complex128 or tuple(T.shape) != (k, n) or not T.is_contiguous():
+            raise TypeError("bse: Xt, Yt must be contiguous complex128 tensors of shape (k, n)")
+    info = _Info()
+    code = lib().bse_solve_chol_noalloc(n, int(k), _P(A.data_ptr()), _P(B.data_ptr()), _P(omega.data_ptr()),
+                                        _P(Xt.data_ptr()), _P(Yt.data_ptr()), ctypes.byref(info),
+                                        _P(_stream_ptr(stream)))
+    if code != OK:
+        msg = (f"n = {n} above the allocation-free limit {NOALLOC_MAX_N}" if code == 10
+               else "allocation-free solve failed")
+        raise BseError(code, msg, info.info)
+    return omega, Xt.mT, Yt.mT
 
 def solve_host(A, B, method: str = "chol", il: int | None = None, iu: int | None = None, handle: Handle | None = None,
                stream=None):

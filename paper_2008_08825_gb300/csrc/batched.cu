@@ -839,3 +839,42 @@ void batched_fill_desc(void* slot, int64_t n, int64_t k, const void* A, const vo
   d.ws = ws, d.status = status;
   *(BatchDesc*)slot = d;
 }
+
+// ---- one instance, no allocation ----------------------------------------------
+// The Cholesky pipeline of ONE instance (the same device routines as
+// batched_chol_kernel) with its parameters passed by value and its workspace
+// and two status words in scratch memory the caller hands in: no queue
+// counter and no descriptor table, so the host needs no device allocation
+// for it.  The status words must start at zero; the kernel clears them
+// itself before use.
+__global__ void __launch_bounds__(BT, 1) single_chol_kernel(BatchDesc d) {
+  extern __shared__ cplx dyn[];
+  cplx* vs = dyn;                    // 1024
+  cplx* wsv = dyn + 1024;            // 1024
+  cplx* S = dyn + 2048;              // CNB x CLD
+  cplx* Iv = S + CNB * CLD;          // CNB x CLD
+  __shared__ double red[BT / 32];
+  __shared__ int flag;
+  if (threadIdx.x == 0) {
+    d.status[0] = 0;
+    d.status[1] = 0;
+  }
+  __threadfence_block();
+  __syncthreads();
+  solve_instance(d, vs, wsv, red, S, Iv, &flag);
+}
+
+cudaError_t single_chol_prepare() {
+  return cudaFuncSetAttribute(single_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)batched_smem_bytes());
+}
+
+cudaError_t single_chol_launch(cudaStream_t s, int64_t n, int64_t k, const void* A, const void* B, double* omega,
+                               void* X, void* Y, char* ws, int64_t* status) {
+  BatchDesc d;
+  d.n = n, d.k = k, d.A = (const cplx*)A, d.B = (const cplx*)B, d.omega = omega, d.X = (cplx*)X, d.Y = (cplx*)Y;
+  d.ws = ws, d.status = status;
+  single_chol_kernel<<<1, BT, batched_smem_bytes(), s>>>(d);
+  bse_count_launch();
+  return cudaGetLastError();
+}

@@ -122,6 +122,9 @@ size_t batched_desc_bytes();
 void batched_fill_desc(void* slot, int64_t n, int64_t k, const void* A, const void* B, double* omega, void* X,
                        void* Y, char* ws, int64_t* status);
 size_t batched_svd_inst_bytes(int64_t n, int64_t k);
+cudaError_t single_chol_prepare();
+cudaError_t single_chol_launch(cudaStream_t s, int64_t n, int64_t k, const void* A, const void* B, double* omega,
+                               void* X, void* Y, char* ws, int64_t* status);
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid,
                                int method);
 
