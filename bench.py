@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=768)
     ap.add_argument("--methods", default="chol,svd", help="comma list of chol, svd")
     ap.add_argument("--precisions", default="fp64,mixed", help="fp64 (headline) and/or mixed")
+    ap.add_argument("--no-values-only", action="store_true", help="skip the eigenvalues-only timings")
+    ap.add_argument("--compare-sqrt", action="store_true",
+                    help="also time Alg. 1 (SQRT) against Alg. 2 (CHOL), one warm solve each")
     ap.add_argument("--kernel-profile", action="store_true",
                     help="instead of timing steps: one warm solve per method and precision with per-kernel "
                          "event profiling (library profiling level 2), one JSON line each")
@@ -112,9 +115,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SMS, SM_MAX_MHZ, FP64_FLOPS_PER_CLK_SM = 152, 2070.0, 4.0  # 2 DFMA per clock per SM
+
+
 def fp64_peak():
-    """Measured FP64 DFMA throughput of this part (profiles/fp64_peaks_gb300.md)."""
-    return 1200.0  # GFLOP/s -> reported in TFLOP/s below
+    """FP64 FMA-pipe peak derived from the unit counts and clocks: 152 SMs x
+    2070 MHz x 4 flops per clock per SM = 1258.6 GFLOP/s (the part's nominal
+    1.25 TFLOP/s FP64).  A DFMA-only loop measured 1200 GFLOP/s on this GB300
+    (profiles/fp64_peaks_gb300.md)."""
+    return SMS * SM_MAX_MHZ * FP64_FLOPS_PER_CLK_SM / 1e3  # GFLOP/s
 
 
 def cpu_baseline(n_sample: int, steps: int = 1):
@@ -160,56 +169,101 @@ def run_reference(args, rank):
 
 
 def run_batched(args, rank, world, local):
-    """512 instances, n log-uniform in [32, 1024] (seed 10000), instance i from
-    the base generator with seed i; the lowest 32 eigenpairs of each (Alg. 2)
-    in one persistent launch, against the same instances solved one at a time
-    by the single-instance path (subset solves, il = 1, iu = 32)."""
+    """The batched workload: 512 instances per GPU, n log-uniform in [32, 1024]
+    (seed 10000), instance i from the base generator with seed i; the lowest
+    32 eigenpairs of each in one persistent launch per rank.  With N ranks the
+    batch is 512 N instances dealt to the ranks by the cost-balanced greedy
+    rule on n^3 (shard.py): no exchange on the data path, weak scaling.
+    Alg. 2 is the headline; Alg. 3 is reported beside it.  The same instances
+    through the single-instance solver one by one give the batching speed-up."""
     import torch
 
-    from paper_2008_08825_gb300 import bse, inputs
+    from paper_2008_08825_gb300 import bse, inputs, shard
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sizes = inputs.batched_sizes()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    per_gpu = 512
+    sizes = inputs.batched_sizes(count=per_gpu * world)
+    mine = shard.partition_by_cost(sizes, world)[rank]
     inst = []
-    for i, n in enumerate(sizes):
-        A, B = inputs.base(int(n), seed=i + 100000 * rank)
+    for i in mine:
+        A, B = inputs.base(int(sizes[i]), seed=int(i))
         inst.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
     h = bse.Handle()
-    bt = bse.Batch(inst, k=32)
-    for _ in range(args.warmup):
-        bt.run(handle=h)
     stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = h.launches()
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        bt.run(handle=h)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    t_batch = ev0.elapsed_time(ev1) / 1e3 / args.steps
-    launches = (h.launches() - l0) // args.steps
-    # the same instances through the single-instance solver
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for A, B in inst:
-        bse.solve(A, B, method="chol", il=1, iu=min(32, A.shape[0]), handle=h)
-    torch.cuda.synchronize()
-    t_loop = time.perf_counter() - t0
+    methods = [m for m in args.methods.split(",") if m]
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for method in methods:
+        bt = bse.Batch(inst, k=32, method=method)
+        for _ in range(args.warmup):
+            bt.run(handle=h)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = h.launches()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bt.run(handle=h)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        t_batch = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps)
+        launches = (h.launches() - l0) // args.steps
+        statuses = shard.gather_to_rank0({i: s for i, s in zip(mine, bt.status)}, dist)
+        # the same instances through the single-instance solver
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for A, B in inst:
+            bse.solve(A, B, method=method, il=1, iu=min(32, A.shape[0]), handle=h)
+        torch.cuda.synchronize()
+        t_loop = max_over_ranks(time.perf_counter() - t0)
+        results[method] = (t_batch, t_loop, launches, ck, statuses)
     e_n3 = float(np.mean(sizes.astype(np.float64) ** 3))
-    flops = len(sizes) * (4.0 / 3.0 + 16.0 / 3.0 + 16.0 / 3.0) * e_n3  # Cholesky, congruence, reduction (real)
+    # Cholesky(s), congruence or product, reduction, k back-transformed vectors omitted (O(n^2 k))
+    flops_per_n3 = {"chol": 4.0 / 3.0 + 16.0 / 3.0 + 16.0 / 3.0, "svd": 8.0 / 3.0 + 8.0 / 3.0 + 32.0 / 3.0}
     if rank == 0:
-        line = {"metric": "batched BSE solves/sec (512 instances, n in [32,1024], lowest 32 pairs, FP64)",
-                "value": len(sizes) / t_batch, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "512 BSE instances, n = round(exp(U[ln 32, ln 1024])), base generator, "
-                                       "lowest 32 eigenpairs (Alg. 2), one persistent launch", "instances": len(sizes),
-                           "k": 32, "parallelism": "replicas"},
-                "single_instance_loop_s": t_loop, "speedup_vs_single_instance_loop": t_loop / t_batch,
-                "model_tflops": flops / t_batch / 1e12, "gpu_launches": launches}
+        def entry(method):
+            t_batch, t_loop, launches, ck, statuses = results[method]
+            return {"value": len(sizes) / t_batch, "unit": "solves/s", "ms_per_step": t_batch * 1e3,
+                    "single_instance_loop_s": t_loop, "speedup_vs_single_instance_loop": t_loop / t_batch,
+                    "model_tflops": len(sizes) * flops_per_n3[method] * e_n3 / t_batch / 1e12,
+                    "gpu_launches": launches, "clocks": ck,
+                    "failed_instances": sum(1 for v in statuses.values() if v != 0)}
+        head = entry(methods[0])
+        line = {"metric": f"batched BSE solves/sec ({per_gpu} instances per GPU, n in [32,1024], lowest 32 pairs, "
+                          "FP64)",
+                "value": head.pop("value"), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head.pop("ms_per_step"), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{len(sizes)} BSE instances, n = round(exp(U[ln 32, ln 1024])), base "
+                                       f"generator, lowest 32 eigenpairs (Alg. {2 if methods[0] == 'chol' else 3}), "
+                                       "one persistent launch per GPU, instances dealt by n^3 cost",
+                           "instances": len(sizes), "k": 32, "parallelism": f"shard{world}",
+                           "l2": "working set (inputs and workspaces, several GB per GPU) larger than L2"},
+                **head}
+        for m in methods[1:]:
+            line[m] = entry(m)
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_kernel_profile(args, local):
@@ -355,6 +409,31 @@ def main():
         nm = len(methods)
         e2e = {"value": nm * world / te, "unit": "solves/s", "h2d_bytes_per_step": nm * 2 * n * n * 16,
                "d2h_bytes_per_step": nm * (n * 8 + 2 * n * n * 16)}
+
+    def one_solve(method, vectors):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bse.solve(At, Bt, method=method, precision=precs[0], vectors=vectors, handle=h)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    # eigenvalues only (all n; no orthogonalisation, back-transformation or
+    # post-processing): one solve per method, workspace and kernels already warm
+    values_only = None
+    if not args.no_values_only:
+        values_only = {"seconds_per_solve": {m: one_solve(m, False) for m in methods},
+                       "what": "all n eigenvalues, no eigenvectors, same workload and precision"}
+    sqrt_cmp = None
+    if args.compare_sqrt:
+        h.reserve(n, "sqrt", dev, precs[0])
+        one_solve("sqrt", True)
+        t_sqrt = one_solve("sqrt", True)
+        t_chol = one_solve("chol", True)
+        sqrt_cmp = {"sqrt_s": t_sqrt, "chol_s": t_chol, "chol_over_sqrt": t_chol / t_sqrt,
+                    "model_ratio_table2": (40.0 / 3.0) / (86.0 / 3.0),
+                    "what": "Alg. 1 vs Alg. 2, all n eigenpairs with vectors, one warm solve each"}
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -367,8 +446,10 @@ def main():
         "achieved": gemm_tf, "peak": peak_tf, "unit": "TFLOP/s",
         "frac": (gemm_tf / peak_tf) if gemm_tf else None,
         "traffic": None,
-        "peak_source": "FP64 DFMA throughput measured on this GB300 (profiles/fp64_peaks_gb300.md); "
-                       "FP64 mma.sync measured lower (1.05 TFLOP/s)",
+        "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flops/clock/SM (nominal FP64 1.25 TFLOP/s); "
+                       "a DFMA loop measured 1.20 TFLOP/s and FP64 mma.sync 1.05 TFLOP/s on this GB300 "
+                       "(profiles/fp64_peaks_gb300.md)",
+        "measured_dfma_peak": 1.20,
         "gemm_share_of_step": prof["gemm_ms"] / tot_stage,
         "gemm_launches": prof["gemm_launches"],
     }
@@ -391,6 +472,10 @@ def main():
         "stage_ms_per_step": {k: v / args.steps for k, v in zip(stage_names, prof["stage_ms"]) if v > 0},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cb,
     }
+    if values_only:
+        line["values_only"] = values_only
+    if sqrt_cmp:
+        line["sqrt_vs_chol"] = sqrt_cmp
     if "mixed" in results and precs[0] != "mixed":
         el_m, l_m, pr_m, ck_m, om_m = results["mixed"]
         diff = max(float(np.max(np.abs(a - b) / b)) for a, b in zip(om_m, om_head))

@@ -53,7 +53,8 @@ typedef enum {
 } bse_status;
 
 typedef enum { BSE_PREC_FP64 = 0, BSE_PREC_MIXED = 1 } bse_precision;
-typedef enum { BSE_METHOD_CHOL = 0, BSE_METHOD_SVD = 1 } bse_method;
+/* BSE_METHOD_TDA only names the workspace of bse_solve_tda in bse_workspace_size */
+typedef enum { BSE_METHOD_CHOL = 0, BSE_METHOD_SVD = 1, BSE_METHOD_SQRT = 2, BSE_METHOD_TDA = 3 } bse_method;
 
 typedef struct bse_info {
   int64_t info;          /* failing column (1-based) for NOT_PD, else 0 */
@@ -89,10 +90,11 @@ typedef enum {
    * FMA engine, larger ones use the split-operand tensor-core engine
    * (default 1 << 24).  1 sends every product through the tensor cores. */
   BSE_OPT_TC_MIN_MNK = 1,
-  /* Batched solves: resident CTAs per SM of the persistent kernel, 1 or 2
-   * (default 2).  One CTA per SM gives each instance the SM's whole FP64
-   * pipe (shorter critical path for the largest instances); two hide more
-   * latency.  Chosen per workload by the autotuner (autotune.py). */
+  /* Batched solves: CTAs per SM in the persistent kernel's grid, 1 or 2
+   * (default 1).  One CTA per SM gives each instance the SM's whole FP64
+   * pipe and registers (shorter critical path for the largest instances);
+   * two hide more latency where registers allow two resident CTAs.  Chosen
+   * per workload by the autotuner (autotune.py). */
   BSE_OPT_BATCH_CTAS_PER_SM = 2
 } bse_option;
 bse_status bse_set_option(bse_handle h, int option, int64_t value);
@@ -144,6 +146,41 @@ bse_status bse_solve_svd(bse_handle h, int64_t n, const double* A, int64_t lda, 
                          int64_t ldx, double* Y, int64_t ldy, bse_info* info, void* stream);
 
 /*
+ * Square-root method, Alg. 1 (Section 3.1), the established approach the
+ * paper compares against (Table 2: 28 2/3 n^3 flops against 13 1/3 for
+ * Alg. 2):
+ *   S = (A - B)^{1/2} = Q D^{1/2} Q^H from the eigendecomposition
+ *   A - B = Q D Q^H;  M = S (A + B) S;  M V_M = V_M D_M;  Lambda = D_M^{1/2};
+ *   V1 = S^{-1} V_M Lambda^{1/2};  V2 = S V_M Lambda^{-1/2};
+ *   X = (V1 + V2)/2,  Y = (V2 - V1)/2.
+ * Arguments, precisions and errors as for bse_solve_chol, except that
+ * BSE_ERR_NOT_PD_AMINUSB reports in info the 1-based index (ascending) of a
+ * non-positive eigenvalue of A - B, and a non-positive eigenvalue of M gives
+ * BSE_ERR_NOT_PD_APLUSB (info 0).  The profiler's stage 1 covers the square
+ * root (eigensolve of A - B, S and S^{-1}).
+ */
+bse_status bse_solve_sqrt(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X,
+                          int64_t ldx, double* Y, int64_t ldy, bse_info* info, void* stream);
+
+/*
+ * Tamm-Dancoff approximation, B = 0 (Section 4, the TDA remark on the LiF
+ * example): H1 = [A 0; 0 -A], so omega are the eigenvalues of A (ascending)
+ * and the eigenvector of omega_i is [x_i; 0] with x_i^H x_i = 1; Y is not
+ * materialised.  One Householder reduction of A, the tridiagonal solve and
+ * one back-transformation (the eigensolve of Alg. 2 step 2 applied to A).
+ * A        device, n x n Hermitian, lower triangle read; must be positive
+ *          definite (else BSE_ERR_NOT_PD_APLUSB, info 0).
+ * il, iu   1-based inclusive range into the ascending omega.
+ * omega    device, k = iu - il + 1 doubles.
+ * X        device, n x k complex, leading dimension ldx; NULL for
+ *          eigenvalues only.
+ * FP64 arithmetic throughout.
+ */
+bse_status bse_solve_tda(bse_handle h, int64_t n, const double* A, int64_t lda, int64_t il, int64_t iu,
+                         double* omega, double* X, int64_t ldx, bse_info* info, void* stream);
+
+/*
  * Gradient of L = sum_i w_i omega_i with respect to Hermitian A and B.
  * Thm. 3 item 3 (left eigenvector of H1 is v^H Sigma) with the
  * Sigma-normalisation of Eq. (13) give d omega_i = v_i^H [dA dB; dB dA] v_i,
@@ -159,8 +196,9 @@ bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t
                     void* stream);
 
 /*
- * End-to-end variant: identical to bse_solve_chol (method = BSE_METHOD_CHOL)
- * or bse_solve_svd (BSE_METHOD_SVD), but every data pointer (A, B, omega, X,
+ * End-to-end variant: identical to bse_solve_chol (method = BSE_METHOD_CHOL),
+ * bse_solve_svd (BSE_METHOD_SVD) or bse_solve_sqrt (BSE_METHOD_SQRT), but
+ * every data pointer (A, B, omega, X,
  * Y) is a HOST pointer.  The library copies A and B to device workspace
  * (pinned host memory gives full PCIe/C2C bandwidth), solves, and copies
  * omega, X, Y back before returning.
@@ -219,7 +257,8 @@ int64_t bse_launch_count(bse_handle h);
  * (the solves already synchronise their stream, so no extra sync happens).
  */
 #define BSE_NSTAGES 10
-/* stage index: 0 form A+-B, 1 Cholesky, 2 congruence / product L1^H L2,
+/* stage index: 0 form A+-B, 1 Cholesky (square root for Alg. 1),
+ * 2 congruence / product L1^H L2,
  * 3 Householder reduction, 4 tridiagonal eigensolve, 5 orthogonalisation,
  * 6 back-transformation, 7 post-processing + final setup, 8 gradient,
  * 9 refinement (mixed form) */

@@ -38,7 +38,7 @@ STATUS_NAMES = {
     10: "BSE_ERR_TOO_LARGE",
 }
 NOALLOC_MAX_N = 256
-METHODS = {"chol": 0, "svd": 1}
+METHODS = {"chol": 0, "svd": 1, "sqrt": 2, "tda": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 
@@ -72,9 +72,10 @@ def _bind(lib):
     lib.bse_last_error.restype = ctypes.c_char_p
     lib.bse_workspace_size.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     lib.bse_set_workspace.argtypes = [_P, _P, ctypes.c_size_t]
-    for f in (lib.bse_solve_chol, lib.bse_solve_svd):
+    for f in (lib.bse_solve_chol, lib.bse_solve_svd, lib.bse_solve_sqrt):
         f.argtypes = [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _I64, _P, _I64,
                       ctypes.POINTER(_Info), _P]
+    lib.bse_solve_tda.argtypes = [_P, _I64, _P, _I64, _I64, _I64, _P, _P, _I64, ctypes.POINTER(_Info), _P]
     lib.bse_grad.argtypes = [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _I64, _P, _I64, _P]
     lib.bse_solve_host.argtypes = [_P, ctypes.c_int, _I64, _P, _I64, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P,
                                    _I64, _P, _I64, ctypes.POINTER(_Info), _P]
@@ -200,7 +201,8 @@ def _colmajor(A: torch.Tensor) -> torch.Tensor:
 def solve(A: torch.Tensor, B: torch.Tensor, method: str = "chol", precision: str = "fp64", il: int | None = None,
           iu: int | None = None, vectors: bool = True, handle: Handle | None = None, stream=None):
     """Positive eigenvalues omega (ascending) and Sigma-normalised eigenvectors
-    [X; Y] of H1 = [A B; -B -A] (Alg. 2 for method='chol', Alg. 3 for 'svd').
+    [X; Y] of H1 = [A B; -B -A] (Alg. 2 for method='chol', Alg. 3 for 'svd',
+    Alg. 1, the square-root method, for 'sqrt').
 
     Returns (omega, X, Y) with omega of shape (k,), X, Y of shape (n, k)
     (None when vectors=False), k = iu - il + 1 (1-based, inclusive; default all).
@@ -221,7 +223,7 @@ def solve(A: torch.Tensor, B: torch.Tensor, method: str = "chol", precision: str
         Xt = Yt = None
         px = py = None
     info = _Info()
-    fn = lib().bse_solve_chol if method == "chol" else lib().bse_solve_svd
+    fn = {"chol": lib().bse_solve_chol, "svd": lib().bse_solve_svd, "sqrt": lib().bse_solve_sqrt}[method]
     code = fn(h.ptr, n, _P(Ac.data_ptr()), max(n, 1), _P(Bc.data_ptr()), max(n, 1), il, iu, PRECISIONS[precision],
               _P(omega.data_ptr()), px, max(n, 1), py, max(n, 1), ctypes.byref(info), _P(_stream_ptr(stream)))
     _check(code, info.info)
@@ -259,6 +261,28 @@ def solve_noalloc(A: torch.Tensor, B: torch.Tensor, k: int, omega: torch.Tensor,
                else "allocation-free solve failed")
         raise BseError(code, msg, info.info)
     return omega, Xt.mT, Yt.mT
+
+
+def solve_tda(A: torch.Tensor, il: int | None = None, iu: int | None = None, vectors: bool = True,
+              handle: Handle | None = None, stream=None):
+    """Tamm-Dancoff approximation (B = 0): omega = eigenvalues of the Hermitian
+    positive definite A (ascending, 1-based inclusive range [il, iu]) and the
+    unit eigenvectors X (n x k); the Y half of [X; Y] is zero."""
+    n = A.shape[0]
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    k = max(iu - il + 1, 0)
+    h = handle or default_handle()
+    h.reserve(n, "tda", A.device)
+    Ac = _colmajor(A)
+    omega = torch.empty(k, dtype=torch.float64, device=A.device)
+    Xt = torch.empty((k, n), dtype=torch.complex128, device=A.device) if vectors else None
+    info = _Info()
+    code = lib().bse_solve_tda(h.ptr, n, _P(Ac.data_ptr()), max(n, 1), il, iu, _P(omega.data_ptr()),
+                               _P(Xt.data_ptr()) if vectors else None, max(n, 1), ctypes.byref(info),
+                               _P(_stream_ptr(stream)))
+    _check(code, info.info)
+    return omega, (Xt.mT if vectors else None)
 
 def solve_host(A, B, method: str = "chol", il: int | None = None, iu: int | None = None, handle: Handle | None = None,
                stream=None):

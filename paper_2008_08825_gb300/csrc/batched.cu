@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(BT, 1) batched_svd_kernel(const BatchDesc* __r
   }
 }
 
-__global__ void __launch_bounds__(BT, 2) batched_chol_kernel(const BatchDesc* __restrict__ desc, int64_t count,
+__global__ void __launch_bounds__(BT, 1) batched_chol_kernel(const BatchDesc* __restrict__ desc, int64_t count,
                                                              int* counter) {
   extern __shared__ cplx dyn[];
   cplx* vs = dyn;                    // 1024

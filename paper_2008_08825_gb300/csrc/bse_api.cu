@@ -50,7 +50,7 @@ struct bse_context {
   size_t bdesc_bytes = 0;
   int sms = 0;
   int64_t oz_min = (int64_t)1 << 24;
-  int batch_cps = 2;
+  int batch_cps = 1;
 };
 
 // Makes the handle's profiler current for this thread for one entry point;
@@ -204,14 +204,92 @@ static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k, int prec) {
   b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
 }
 
+// Alg. 1: M1 = A + B (full), A - B reduced in M, its eigenvectors Q, the square
+// root S and its inverse Si, a product buffer T; the reduction and tridiagonal
+// work serve both eigensolves (all n vectors for the square root).
+struct SqrtBuffers {
+  void* oz;
+  RefineBufs rf;
+  int64_t* status;
+  cplx *M1, *M, *Q, *S, *Si, *T;
+  HetrdWork h;
+  TriPlan t;
+  double *Z, *d2, *qp, *qm, *lam, *c1, *c2;
+  cplx* tmp;
+};
+
+static void carve_sqrt(Plan& pl, SqrtBuffers& b, int64_t n, int64_t k, int prec) {
+  const int nbt = hetrd_panel();
+  b.oz = prec == BSE_PREC_MIXED ? pl.take<char>(oz_work_bytes(n, 8)) : nullptr;
+  carve_refine(pl, b.rf, n, k, prec);
+  b.status = pl.take<int64_t>(4);
+  b.M1 = pl.take<cplx>((size_t)n * n);
+  b.M = pl.take<cplx>((size_t)n * n);
+  b.Q = pl.take<cplx>((size_t)n * n);
+  b.S = pl.take<cplx>((size_t)n * n);
+  b.Si = pl.take<cplx>((size_t)n * n);
+  b.T = pl.take<cplx>((size_t)n * n);
+  b.h.V = pl.take<cplx>((size_t)n * n);
+  b.h.W = pl.take<cplx>((size_t)n * nbt);
+  b.h.tau = pl.take<cplx>(n);
+  b.h.d = pl.take<double>(n);
+  b.h.e = pl.take<double>(n);
+  b.h.part = pl.take<cplx>(hetrd_part_elems(n));
+  b.h.small = pl.take<cplx>(4 * nbt * nbt + 64);
+  b.t.carve(pl, n, n);
+  b.Z = pl.take<double>((size_t)n * n);
+  b.d2 = pl.take<double>(n);
+  b.qp = pl.take<double>(n);
+  b.qm = pl.take<double>(n);
+  b.lam = pl.take<double>(k);
+  b.c1 = pl.take<double>(k);
+  b.c2 = pl.take<double>(k);
+  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * n);
+}
+
+// Tamm-Dancoff (B = 0): the Hermitian eigenproblem of A alone
+struct TdaBuffers {
+  int64_t* status;
+  cplx* M;
+  HetrdWork h;
+  TriPlan t;
+  double *Z, *lam, *c1, *c2;
+  cplx* tmp;
+};
+
+static void carve_tda(Plan& pl, TdaBuffers& b, int64_t n, int64_t k) {
+  const int nbt = hetrd_panel();
+  b.status = pl.take<int64_t>(4);
+  b.M = pl.take<cplx>((size_t)n * n);
+  b.h.V = pl.take<cplx>((size_t)n * n);
+  b.h.W = pl.take<cplx>((size_t)n * nbt);
+  b.h.tau = pl.take<cplx>(n);
+  b.h.d = pl.take<double>(n);
+  b.h.e = pl.take<double>(n);
+  b.h.part = pl.take<cplx>(hetrd_part_elems(n));
+  b.h.small = pl.take<cplx>(4 * nbt * nbt + 64);
+  b.t.carve(pl, n, k);
+  b.Z = pl.take<double>((size_t)n * k);
+  b.lam = pl.take<double>(k);
+  b.c1 = pl.take<double>(k);
+  b.c2 = pl.take<double>(k);
+  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
+}
+
 static size_t plan_bytes(int64_t n, int64_t k, int method, int prec) {
   Plan pl(nullptr);
   if (method == BSE_METHOD_CHOL) {
     CholBuffers b;
     carve_chol(pl, b, n, k, prec);
-  } else {
+  } else if (method == BSE_METHOD_SVD) {
     SvdBuffers b;
     carve_svd(pl, b, n, k, prec);
+  } else if (method == BSE_METHOD_SQRT) {
+    SqrtBuffers b;
+    carve_sqrt(pl, b, n, k, prec);
+  } else {
+    TdaBuffers b;
+    carve_tda(pl, b, n, k);
   }
   return pl.off + 256;
 }
@@ -468,6 +546,142 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
 
 // ---------------------------------------------------------------------------
 // Batched solves.
+// Alg. 1 (square-root method): S = (A - B)^{1/2} from the eigendecomposition
+// A - B = Q diag(d) Q^H; M = S (A + B) S; M V_M = V_M D; Lambda = D^{1/2};
+// V1 = S^{-1} V_M Lambda^{1/2}, V2 = S V_M Lambda^{-1/2}; X, Y as in Alg. 2.
+static bse_status solve_sqrt_dev(bse_context* h, int64_t n, const cplx* A, int64_t lda, const cplx* B, int64_t ldb,
+                                 int64_t il, int64_t iu, int prec, double* omega, cplx* X, int64_t ldx, cplx* Y,
+                                 int64_t ldy, bse_info* info, cudaStream_t s) {
+  const int64_t k = iu - il + 1;
+  void* ws;
+  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_SQRT, prec), &ws));
+  Plan pl(ws);
+  SqrtBuffers b;
+  carve_sqrt(pl, b, n, k, prec);
+  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min});
+  int64_t* st = b.status;
+  BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  ProfGuard pgd(h, s);
+  {
+    StageScope sc(0, s);
+    TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.M1, n, 1));
+    TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.M, n, 0));
+    if (b.rf.F1 && X) {
+      TRY(form_sum(s, n, A, lda, B, ldb, +1.0, b.rf.F1, n, 1));
+      TRY(form_sum(s, n, A, lda, B, ldb, -1.0, b.rf.F2, n, 1));
+    }
+  }
+  {
+    // the square root of A - B (Alg. 1 step 1): a full Hermitian eigensolve
+    StageScope sc(1, s);
+    TRY(hetrd_lower(s, n, b.M, n, b.h, st));
+    TRY(tridiag_eig(s, n, b.h.d, b.h.e, 0, 0, n - 1, b.d2, b.Z, n, b.t.w, st));
+    TRY(orthonormalize_columns(s, n, n, b.Z, n, b.t.w, st));
+    TRY(real_to_complex(s, n, n, b.Z, n, b.Q, n));
+    TRY(hetrd_backtransform(s, n, n, b.h, b.Q, n, b.tmp, st));
+    TRY(sqrt_factors(s, n, b.d2, b.qp, b.qm, st));
+    TRY(scale_columns(s, n, n, b.Q, n, b.qp, b.T, n));
+    GemmParams<cplx> ps = gemm_params<cplx>(n, n, n, OPN, b.T, n, OPC, b.T, n, one, zero, b.S, n);
+    ps.lowerC = 1;
+    ps.status = st;
+    TRY(gemm_z(s, ps));
+    TRY(hermitian_fill_upper(s, n, b.S, n));
+    TRY(scale_columns(s, n, n, b.Q, n, b.qm, b.T, n));
+    GemmParams<cplx> pi = gemm_params<cplx>(n, n, n, OPN, b.T, n, OPC, b.T, n, one, zero, b.Si, n);
+    pi.lowerC = 1;
+    pi.status = st;
+    TRY(gemm_z(s, pi));
+    TRY(hermitian_fill_upper(s, n, b.Si, n));
+  }
+  {
+    // M = S (A + B) S (lower), into M
+    StageScope sc(2, s);
+    GemmParams<cplx> p1 = gemm_params<cplx>(n, n, n, OPN, b.M1, n, OPN, b.S, n, one, zero, b.T, n);
+    p1.status = st;
+    TRY(gemm_z(s, p1));
+    GemmParams<cplx> p2 = gemm_params<cplx>(n, n, n, OPN, b.S, n, OPN, b.T, n, one, zero, b.M, n);
+    p2.lowerC = 1;
+    p2.status = st;
+    TRY(gemm_z(s, p2));
+  }
+  {
+    StageScope sc(3, s);
+    TRY(hetrd_lower(s, n, b.M, n, b.h, st));
+  }
+  {
+    StageScope sc(4, s);
+    TRY(tridiag_eig(s, n, b.h.d, b.h.e, 0, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, n, b.t.w, st));
+    TRY(finish_omega(s, k, b.lam, 0, omega, b.c1, b.c2, st));
+  }
+  if (!X) return finish(h, s, st, info);
+  {
+    StageScope sc(5, s);
+    TRY(orthonormalize_columns(s, n, k, b.Z, n, b.t.w, st));
+  }
+  cplx* VM = b.Q;  // reuse: V_M (n x k)
+  {
+    StageScope sc(6, s);
+    TRY(real_to_complex(s, n, k, b.Z, n, VM, n));
+    TRY(hetrd_backtransform(s, n, k, b.h, VM, n, b.tmp, st));
+  }
+  StageScope sc7(7, s);
+  // P = S^{-1} V_M (V1 unscaled) into T; X, Y from P and S V_M (V2 unscaled)
+  GemmParams<cplx> p3 = gemm_params<cplx>(n, k, n, OPN, b.Si, n, OPN, VM, n, one, zero, b.T, n);
+  p3.status = st;
+  TRY(gemm_z(s, p3));
+  GemmParams<cplx> p4 = gemm_params<cplx>(n, k, n, OPN, b.S, n, OPN, VM, n, one, zero, X, ldx);
+  p4.status = st;
+  p4.epi = EPI_XY;
+  p4.P = b.T, p4.ldp = n, p4.c1 = b.c1, p4.c2 = b.c2, p4.Y = Y, p4.ldy = ldy;
+  TRY(gemm_z(s, p4));
+  if (b.rf.F1) {
+    StageScope scr(9, s);
+    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st));
+    return finish(h, s, st, info, b.rf.est_max);
+  }
+  return finish(h, s, st, info);
+}
+
+// Tamm-Dancoff approximation (B = 0): omega = eig(A) (ascending, positive),
+// X = the unit eigenvectors of A, Y = 0 (not materialised).
+static bse_status solve_tda_dev(bse_context* h, int64_t n, const cplx* A, int64_t lda, int64_t il, int64_t iu,
+                                double* omega, cplx* X, int64_t ldx, bse_info* info, cudaStream_t s) {
+  const int64_t k = iu - il + 1;
+  void* ws;
+  TRY(ensure_ws(h, plan_bytes(n, k, BSE_METHOD_TDA, BSE_PREC_FP64), &ws));
+  Plan pl(ws);
+  TdaBuffers b;
+  carve_tda(pl, b, n, k);
+  int64_t* st = b.status;
+  BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
+  ProfGuard pgd(h, s);
+  {
+    StageScope sc(0, s);
+    TRY(form_sum(s, n, A, lda, A, lda, 0.0, b.M, n, 0));
+  }
+  {
+    StageScope sc(3, s);
+    TRY(hetrd_lower(s, n, b.M, n, b.h, st));
+  }
+  {
+    StageScope sc(4, s);
+    TRY(tridiag_eig(s, n, b.h.d, b.h.e, 0, il - 1, iu - 1, b.lam, X ? b.Z : nullptr, n, b.t.w, st));
+    TRY(finish_omega(s, k, b.lam, 1, omega, b.c1, b.c2, st));
+  }
+  if (!X) return finish(h, s, st, info);
+  {
+    StageScope sc(5, s);
+    TRY(orthonormalize_columns(s, n, k, b.Z, n, b.t.w, st));
+  }
+  {
+    StageScope sc(6, s);
+    TRY(real_to_complex(s, n, k, b.Z, n, X, ldx));
+    TRY(hetrd_backtransform(s, n, k, b.h, X, ldx, b.tmp, st));
+  }
+  return finish(h, s, st, info);
+}
+
 static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* n, const double* const* A,
                                   const double* const* B, int64_t k, int method, int prec, double* const* omega,
                                   double* const* X, double* const* Y, int64_t** dstatus_out, int64_t* dstatus_user,
@@ -599,7 +813,8 @@ bse_status bse_destroy(bse_handle h) {
 const char* bse_last_error(void) { return g_err.c_str(); }
 
 bse_status bse_workspace_size(int64_t n, int method, int prec, size_t* bytes) {
-  if (!bytes || n < 0 || (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) || (prec != BSE_PREC_FP64 && prec != BSE_PREC_MIXED))
+  if (!bytes || n < 0 || method < BSE_METHOD_CHOL || method > BSE_METHOD_TDA ||
+      (prec != BSE_PREC_FP64 && prec != BSE_PREC_MIXED))
     return bse_internal_set_error("bad argument to bse_workspace_size"), BSE_ERR_ARG;
   *bytes = plan_bytes(n, n > 0 ? n : 1, method, prec);
   return BSE_OK;
@@ -631,6 +846,27 @@ bse_status bse_solve_svd(bse_handle h, int64_t n, const double* A, int64_t lda, 
                        ldy, info, (cudaStream_t)stream);
 }
 
+bse_status bse_solve_sqrt(bse_handle h, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                          int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx, double* Y,
+                          int64_t ldy, bse_info* info, void* stream) {
+  bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
+  if (r != BSE_OK || n == 0) return r;
+  return solve_sqrt_dev(h, n, (const cplx*)A, lda, (const cplx*)B, ldb, il, iu, prec, omega, (cplx*)X, ldx, (cplx*)Y,
+                        ldy, info, (cudaStream_t)stream);
+}
+
+bse_status bse_solve_tda(bse_handle h, int64_t n, const double* A, int64_t lda, int64_t il, int64_t iu,
+                         double* omega, double* X, int64_t ldx, bse_info* info, void* stream) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  if (n < 0) return bse_internal_set_error("n < 0"), BSE_ERR_ARG;
+  if (n == 0) return BSE_OK;
+  if (!A || !omega) return bse_internal_set_error("NULL A or omega"), BSE_ERR_ARG;
+  if (lda < n) return bse_internal_set_error("lda < n"), BSE_ERR_ARG;
+  if (il < 1 || iu > n || il > iu) return bse_internal_set_error("need 1 <= il <= iu <= n"), BSE_ERR_ARG;
+  if (X && ldx < n) return bse_internal_set_error("ldx < n"), BSE_ERR_ARG;
+  return solve_tda_dev(h, n, (const cplx*)A, lda, il, iu, omega, (cplx*)X, ldx, info, (cudaStream_t)stream);
+}
+
 bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t ldx, const double* Y, int64_t ldy,
                     const double* w, double* dA, int64_t ldda, double* dB, int64_t lddb, void* stream) {
   if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
@@ -649,7 +885,8 @@ bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t
 bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, int64_t lda, const double* B,
                           int64_t ldb, int64_t il, int64_t iu, int prec, double* omega, double* X, int64_t ldx,
                           double* Y, int64_t ldy, bse_info* info, void* stream) {
-  if (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD) return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
+  if (method != BSE_METHOD_CHOL && method != BSE_METHOD_SVD && method != BSE_METHOD_SQRT)
+    return bse_internal_set_error("unknown method"), BSE_ERR_ARG;
   bse_status r = check_common(h, n, A, lda, B, ldb, il, iu, prec, omega, X, ldx, Y, ldy);
   if (r != BSE_OK || n == 0) return r;
   cudaStream_t s = (cudaStream_t)stream;
@@ -677,8 +914,9 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
   if (X) dX = pl.take<cplx>((size_t)n * k), dY = pl.take<cplx>((size_t)n * k);
   BSE_CUDA(cudaMemcpy2DAsync(dA, sizeof(cplx) * n, A, sizeof(cplx) * lda, sizeof(cplx) * n, n, cudaMemcpyHostToDevice, s));
   BSE_CUDA(cudaMemcpy2DAsync(dB, sizeof(cplx) * n, B, sizeof(cplx) * ldb, sizeof(cplx) * n, n, cudaMemcpyHostToDevice, s));
-  r = method == BSE_METHOD_CHOL ? solve_chol_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s)
-                                : solve_svd_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s);
+  r = method == BSE_METHOD_CHOL  ? solve_chol_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s)
+      : method == BSE_METHOD_SVD ? solve_svd_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s)
+                                 : solve_sqrt_dev(h, n, dA, n, dB, n, il, iu, prec, dom, dX, n, dY, n, info, s);
   if (r != BSE_OK) return r;
   BSE_CUDA(cudaMemcpyAsync(omega, dom, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   if (X) {

@@ -344,3 +344,49 @@ bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, co
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
+
+// ---- square-root method (Alg. 1) -----------------------------------------------
+// For the eigenvalues d of A - B: q+ = d^{1/4}, q- = d^{-1/4}, so that with
+// W+- = Q diag(q+-) the principal square root is S = W+ W+^H = Q diag(d^{1/2}) Q^H
+// and its inverse S^{-1} = W- W-^H.  A non-positive eigenvalue means A - B is
+// not positive definite: status (BSE_ERR_NOT_PD_AMINUSB, 1-based index of one
+// such eigenvalue in ascending order).
+__global__ void sqrt_factors_kernel(int64_t n, const double* __restrict__ d, double* __restrict__ qp,
+                                    double* __restrict__ qm, int64_t* status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double di = d[i];
+  if (!(di > 0.0)) {
+    dev_fail(status, BSE_ERR_NOT_PD_AMINUSB, i + 1);
+    return;
+  }
+  const double r = sqrt(sqrt(di));
+  qp[i] = r;
+  qm[i] = 1.0 / r;
+}
+
+bse_status sqrt_factors(cudaStream_t s, int64_t n, const double* d, double* qp, double* qm, int64_t* status) {
+  if (n <= 0) return BSE_OK;
+  sqrt_factors_kernel<<<ceil_div_u(n, 256), 256, 0, s>>>(n, d, qp, qm, status);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+// W(:, j) = Q(:, j) * q[j]
+__global__ void scale_columns_kernel(int64_t n, int64_t k, const cplx* __restrict__ Q, int64_t ldq,
+                                     const double* __restrict__ q, cplx* __restrict__ W, int64_t ldw) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < n && j < k) W[IDX2(i, j, ldw)] = cscale(Q[IDX2(i, j, ldq)], q[j]);
+}
+
+bse_status scale_columns(cudaStream_t s, int64_t n, int64_t k, const cplx* Q, int64_t ldq, const double* q, cplx* W,
+                         int64_t ldw) {
+  if (n <= 0 || k <= 0) return BSE_OK;
+  dim3 grid(ceil_div_u(n, 256), (unsigned)k);
+  scale_columns_kernel<<<grid, 256, 0, s>>>(n, k, Q, ldq, q, W, ldw);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}

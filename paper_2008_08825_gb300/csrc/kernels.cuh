@@ -36,6 +36,9 @@ bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, co
                         double* est_max, const int64_t* status);
 // zero a complex matrix block
 bse_status zero_c(cudaStream_t s, int64_t m, int64_t n, cplx* A, int64_t lda);
+bse_status sqrt_factors(cudaStream_t s, int64_t n, const double* d, double* qp, double* qm, int64_t* status);
+bse_status scale_columns(cudaStream_t s, int64_t n, int64_t k, const cplx* Q, int64_t ldq, const double* q, cplx* W,
+                         int64_t ldw);
 // gradient (Thm. 3 item 3): dA = X W X^H + Y W Y^H, dB = X W Y^H + Y W X^H
 bse_status grad_outer(cudaStream_t s, int64_t n, int64_t k, const cplx* X, int64_t ldx, const cplx* Y,
                       int64_t ldy, const double* w, cplx* dA, int64_t ldda, cplx* dB, int64_t lddb);
