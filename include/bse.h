@@ -95,7 +95,13 @@ typedef enum {
    * pipe and registers (shorter critical path for the largest instances);
    * two hide more latency where registers allow two resident CTAs.  Chosen
    * per workload by the autotuner (autotune.py). */
-  BSE_OPT_BATCH_CTAS_PER_SM = 2
+  BSE_OPT_BATCH_CTAS_PER_SM = 2,
+  /* Mixed form: the tensor-core engine of the split-operand products.
+   * 0 (default): tcgen05.mma with TMEM accumulators, operands staged by TMA
+   * bulk-tensor copies; 1: warp-level mma.sync (the earlier engine, kept for
+   * comparison).  Both give the same FP32 level sums exactly (the combined
+   * set of levels >= 7 up to its rounding). */
+  BSE_OPT_TC_ENGINE = 3
 } bse_option;
 bse_status bse_set_option(bse_handle h, int option, int64_t value);
 

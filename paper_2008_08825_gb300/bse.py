@@ -148,6 +148,10 @@ class Handle:
         """Mixed form: products with m*n*k >= value use the tensor-core engine."""
         _check(lib().bse_set_option(self._h, 1, int(value)))
 
+    def set_tc_engine(self, engine: str) -> None:
+        """Mixed form: 'tcgen05' (default; TMEM accumulators, TMA) or 'mma_sync'."""
+        _check(lib().bse_set_option(self._h, 3, {"tcgen05": 0, "mma_sync": 1}[engine]))
+
     def set_batch_ctas_per_sm(self, value: int) -> None:
         """Batched solves: 1 or 2 resident CTAs per SM for the persistent kernel."""
         _check(lib().bse_set_option(self._h, 2, int(value)))

@@ -132,10 +132,12 @@ bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, 
                                int method);
 
 // ---- ozgemm.cu ----  FP64-accurate complex GEMM on the BF16 tensor cores
+enum { OZ_ENGINE_TCGEN05 = 0, OZ_ENGINE_MMA_SYNC = 1 };
 struct OzWork {
   void* ptr;      // slice / scale workspace (NULL: tensor-core products off)
   size_t bytes;
   int64_t min_mnk;  // products with m*n*k below this stay on the DFMA engine
+  int engine;       // OZ_ENGINE_TCGEN05 (TMEM accumulators, TMA) or OZ_ENGINE_MMA_SYNC
 };
 void oz_set_current(const OzWork& w);
 OzWork oz_current();

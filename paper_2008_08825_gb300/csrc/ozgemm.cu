@@ -22,6 +22,7 @@
 // every 512 k'; levels >= 7 share one FP32 accumulator (their rounding is
 // below 2^-53 of the result).  The dropped pairs (t + u > S + 1) are below
 // 2^-7S of the row/column scale, the same order as FP64 rounding for S = 8.
+#include <cuda.h>
 #include <stdint.h>
 
 #include "kernels.cuh"
@@ -399,6 +400,291 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs<T> z) {
   }
 }
 
+// ---- the tcgen05 product (5th-generation tensor cores, TMEM accumulators) ------
+// Same arithmetic as oz_mma_kernel, tile 128 real rows x 64 real columns:
+//   warp 0      TMA producer: per stage, ONE 3-D bulk-tensor copy brings all S
+//               slices of the A tile (S x 128 rows x 32 k') and one all S
+//               slices of the B tile (S x 64 x 32), 64-byte swizzled;
+//   warp 1      MMA issuer (one thread): per stage and per 16-wide k step, the
+//               36 slice pairs t + u <= S + 1 as tcgen05.mma kind::f16
+//               (BF16 x BF16 -> FP32, M = 128, N = 64) into the TMEM
+//               accumulator of the pair's level set (6 sets x 64 columns);
+//   warp 2      allocates / frees the 512 TMEM columns;
+//   warps 4-7   every 512 k' (the exactness bound of the FP32 level sums) read
+//               the six sets (tcgen05.ld, one row per thread) and add them
+//               into FP64 registers; then the epilogue (scales, alpha/beta,
+//               the fused X/Y setup) straight from registers.
+// Two smem stages of 96 KB; mbarriers full/empty per stage and tmem_full /
+// tmem_empty per fold.  Every wait is bounded: on timeout the CTA records
+// BSE_ERR_TIMEOUT in the status word (when given), stops issuing, drains what
+// it started and frees its TMEM.
+constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 32, UM_STAGES = 2;
+constexpr int UM_SLICE_A = UM_BM * UM_BK * 2, UM_SLICE_B = UM_BN * UM_BK * 2;  // 8 KB, 4 KB
+constexpr long long UM_WAIT_CYCLES = 2000000000LL;                               // about 1 s
+
+template <int S>
+struct UmLayout {
+  static constexpr int A_BYTES = S * UM_SLICE_A, B_BYTES = S * UM_SLICE_B;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int SMEM = UM_STAGES * STAGE + 1024 + 256;  // + alignment, barriers
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// bounded wait on an mbarrier phase; false on timeout (which sets the abort
+// flag) or, when abort_flag is given, as soon as another role has aborted
+__device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                        volatile int* timeout_flag) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (clock64() - t0 > UM_WAIT_CYCLES) {
+      *timeout_flag = 1;
+      return false;
+    }
+  }
+}
+
+// K-major operand tile in shared memory, 64-byte swizzle: rows of 64 bytes,
+// 8-row groups 512 bytes apart (stride byte offset); the leading byte offset
+// is unused for swizzled K-major tiles; descriptor version 1; layout 4 = 64B.
+__device__ __forceinline__ uint64_t um_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N, M
+constexpr uint32_t UM_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_BN >> 3) << 17) | ((uint32_t)(UM_BM >> 4) << 24);
+
+template <int S, typename T>
+__global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ __align__(1024) unsigned char usm[];
+  using L = UmLayout<S>;
+  constexpr bool CPLX = sizeof(T) == sizeof(cplx);
+  constexpr int XF = CPLX ? 2 : 1;
+  const GemmParams<T>& p = z.p;
+  // grouped rasterisation, as in oz_mma_kernel
+  const int64_t gx = gridDim.x, gy = gridDim.y;
+  const int64_t lin = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gx;
+  const int64_t grp = lin / (8 * gx), first = grp * 8;
+  const int64_t rows = (gy - first) < 8 ? (gy - first) : 8;
+  const int64_t loc = lin % (8 * gx);
+  const int64_t ty = first + loc % rows, tx = loc / rows;
+  const int64_t i0 = ty * UM_BM, jr0 = tx * UM_BN, jc0 = jr0 / XF;
+  if (i0 >= p.m || jc0 >= p.n) return;
+  if (p.lowerC && jc0 > i0 + UM_BM - 1) return;
+  if (p.status && *(volatile const int64_t*)p.status) return;
+  int64_t kb = 0, ke = p.k;
+  if (p.triA == TRI_LO) ke = min(ke, i0 + UM_BM);
+  if (p.triA == TRI_UP) kb = max(kb, i0);
+  if (p.triB == TRI_LO) kb = max(kb, jc0);
+  if (p.triB == TRI_UP) ke = min(ke, jc0 + UM_BN / XF);
+  const int64_t kb2 = (XF * kb / UM_BK) * UM_BK, ke2 = XF * ke;
+  const int ntile = ke2 > kb2 ? (int)((ke2 - kb2 + UM_BK - 1) / UM_BK) : 0;
+  const int nfold = (ntile + OZ_FOLD - 1) / OZ_FOLD;
+
+  unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(base + UM_STAGES * L::STAGE);  // full[2] empty[2] tfull tempty drain
+  uint32_t* tslot = (uint32_t*)(bars + 8);
+  int* abort_flag = (int*)(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
+  const uint32_t tfull = smem_u32(bars + 4), tempty = smem_u32(bars + 5), drain = smem_u32(bars + 6);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < UM_STAGES; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * q));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty0 + 8 * q));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(tempty));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(drain));
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  volatile int* ab = abort_flag;
+
+  double acc64[UM_BN];
+#pragma unroll
+  for (int q = 0; q < UM_BN; ++q) acc64[q] = 0.0;
+
+  int issued = 0;  // producer: loads issued
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kt = 0; kt < ntile; ++kt, ++issued) {
+      const int st = kt % UM_STAGES;
+      if (kt >= UM_STAGES && !um_wait(empty0 + 8 * st, ((kt / UM_STAGES) - 1) & 1, ab, ab)) break;
+      const uint32_t fb = full0 + 8 * st;
+      const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
+      const int x = (int)(kb2 + (int64_t)kt * UM_BK);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(L::STAGE) : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+          "[%5];\n" ::"r"(da),
+          "l"(&tmA), "r"(x), "r"((int)i0), "r"(0), "r"(fb)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+          "[%5];\n" ::"r"(db),
+          "l"(&tmB), "r"(x), "r"((int)jr0), "r"(0), "r"(fb)
+          : "memory");
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    uint32_t started = 0;  // bit s: set s written since the last fold
+    for (int kt = 0; kt < ntile && ok; ++kt) {
+      const int st = kt % UM_STAGES;
+      if (kt > 0 && kt % OZ_FOLD == 0) {
+        ok = um_wait(tempty, ((kt / OZ_FOLD) - 1) & 1, ab, ab);
+        if (!ok) break;
+        started = 0;
+      }
+      ok = um_wait(full0 + 8 * st, (kt / UM_STAGES) & 1, ab, ab);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < UM_BK / 16; ++ks) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const uint64_t ad = um_desc(da + t * UM_SLICE_A + ks * 32);
+#pragma unroll
+          for (int u = 0; u < S - t; ++u) {
+            const int lev = t + u;
+            const int set = lev < OZ_NSETS - 1 ? lev : OZ_NSETS - 1;
+            const uint64_t bd = um_desc(db + u * UM_SLICE_B + ks * 32);
+            const uint32_t accum = (started >> set) & 1u;
+            started |= 1u << set;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + set * UM_BN),
+                "l"(ad), "l"(bd), "r"(UM_IDESC), "r"(accum));
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty0 + 8 * st)
+                   : "memory");
+      if ((kt + 1) % OZ_FOLD == 0 || kt + 1 == ntile)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(tfull)
+                     : "memory");
+    }
+  } else if (warp >= 4) {
+    // folds: FP32 level sets -> FP64 registers
+    const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+    for (int f = 0; f < nfold; ++f) {
+      if (!um_wait(tfull, f & 1, ab, ab)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int set = 0; set < OZ_NSETS; ++set) {
+#pragma unroll
+        for (int c0 = 0; c0 < UM_BN; c0 += 16) {
+          uint32_t v[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(tmem + lane_base + set * UM_BN + c0));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc64[c0 + q] += (double)__uint_as_float(v[q]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  const bool failed = *ab != 0;
+  if (warp == 1 && lane == 0) {
+    // every MMA this thread issued has completed once `drain` flips (bounded)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(drain)
+                 : "memory");
+    um_wait(drain, 0, nullptr, ab);
+  }
+  if (failed && warp == 0 && lane == 0) {
+    // the copies still in flight land before the CTA leaves (bounded)
+    for (int kt = issued - UM_STAGES < 0 ? 0 : issued - UM_STAGES; kt < issued; ++kt)
+      um_wait(full0 + 8 * (kt % UM_STAGES), (kt / UM_STAGES) & 1, nullptr, ab);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+  }
+  if (failed) {
+    if (threadIdx.x == 0 && p.status) dev_fail((int64_t*)p.status, BSE_ERR_TIMEOUT, 0);
+    return;
+  }
+  if (warp < 4) return;
+  // epilogue: thread = one row of the tile; complex -- real columns (2j, 2j+1)
+  // are (Re, Im) of logical column jc0 + j; real -- column jc0 + q
+  const int64_t i = i0 + (warp - 4) * 32 + lane;
+  if (i >= p.m) return;
+  const int ei = z.ea[i];
+  if constexpr (CPLX) {
+    const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
+#pragma unroll
+    for (int jj = 0; jj < UM_BN / 2; ++jj) {
+      const int64_t j = jc0 + jj;
+      if (j >= p.n) break;
+      if (p.lowerC && i < j) break;
+      const int fj = z.fb[j];
+      double re = 0.0, im = 0.0;
+      if (ei && fj) {
+        const int sc = (ei - 2048) + (fj - 2048) - 14;
+        re = ldexp(acc64[2 * jj], sc);
+        im = ldexp(acc64[2 * jj + 1], sc);
+      }
+      cplx v = cmul(p.alpha, mkc(re, im));
+      if (p.epi == EPI_XY) {
+        const cplx v1 = p.P[i + j * p.ldp];
+        const double s1 = p.c1[j], s2 = p.c2[j];
+        const cplx x1 = cscale(v1, 0.5 * s1), x2 = cscale(v, 0.5 * s2);
+        p.C[i + j * p.ldc] = cadd(x1, x2);
+        p.Y[i + j * p.ldy] = csub(x2, x1);
+      } else {
+        if (use_beta) v = cadd(v, cmul(p.beta, p.C[i + j * p.ldc]));
+        p.C[i + j * p.ldc] = v;
+      }
+    }
+  } else {
+    const bool use_beta = p.beta != 0.0;
+#pragma unroll
+    for (int jj = 0; jj < UM_BN; ++jj) {
+      const int64_t j = jc0 + jj;
+      if (j >= p.n) break;
+      if (p.lowerC && i < j) break;
+      const int fj = z.fb[j];
+      double v = 0.0;
+      if (ei && fj) v = ldexp(acc64[jj], (ei - 2048) + (fj - 2048) - 14);
+      v *= p.alpha;
+      if (use_beta) v += p.beta * p.C[i + j * p.ldc];
+      p.C[i + j * p.ldc] = v;
+    }
+  }
+}
+
 // ---- real operands -------------------------------------------------------------
 __device__ __forceinline__ bool op_elem_d(const double* X, int64_t ldx, int op, int tri, int64_t r, int64_t c,
                                           int64_t R, int64_t C, double* out) {
@@ -476,7 +762,7 @@ __global__ void oz_split_d_kernel(int64_t R, int64_t C, const double* X, int64_t
 }  // namespace
 
 // Workspace (thread-current, set by the solve entry points)
-static thread_local OzWork g_oz = {nullptr, 0, 0};
+static thread_local OzWork g_oz = {nullptr, 0, 0, OZ_ENGINE_TCGEN05};
 void oz_set_current(const OzWork& w) { g_oz = w; }
 OzWork oz_current() { return g_oz; }
 
@@ -485,6 +771,58 @@ size_t oz_work_bytes(int64_t maxdim, int slices) {
   const int64_t Np = (2 * maxdim + OZ_BN - 1) / OZ_BN * OZ_BN;
   const int64_t Kp = (2 * maxdim + OZ_BK - 1) / OZ_BK * OZ_BK;
   return (size_t)slices * 2 * (size_t)Kp * (size_t)(Mp + Np) + (size_t)(Mp + Np) * 4 + 1024;
+}
+
+// ---- tcgen05 engine: tensor maps and launch ------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// slices [S][rows][Kp] bf16 as a 3-D tensor (k', row, slice); box (32, box_rows, S), 64-byte swizzle
+static bool slice_map(CUtensorMap* m, const void* base, int S, int64_t rows, int64_t Kp, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)UM_BK, (cuuint32_t)box_rows, (cuuint32_t)S};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S, typename T>
+static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_real) {
+  CUtensorMap ta, tb;
+  if (!slice_map(&ta, z.As, S, z.Mp, z.Kp, UM_BM) || !slice_map(&tb, z.Bs, S, z.Np, z.Kp, UM_BN)) {
+    bse_internal_set_error("tensor-core GEMM: cuTensorMapEncodeTiled failed");
+    return BSE_ERR_CUDA;
+  }
+  static bool attr = false;
+  if (!attr) {
+    BSE_CUDA(cudaFuncSetAttribute(oz_umma_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  UmLayout<S>::SMEM));
+    attr = true;
+  }
+  dim3 grid((unsigned)((ncols_real + UM_BN - 1) / UM_BN), (unsigned)((z.Mp + UM_BM - 1) / UM_BM));
+  oz_umma_kernel<S, T><<<grid, 256, UmLayout<S>::SMEM, s>>>(z, ta, tb);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
 }
 
 template <int S>
@@ -514,6 +852,7 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p) {
   BSE_LAUNCH_CHECK();
   OzArgs<cplx> z;
   z.p = p, z.As = As, z.Bs = Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np, z.Kp = Kp;
+  if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, cplx>(s, z, Np);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   static bool attr = false;
   if (!attr) {
@@ -564,6 +903,7 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p) {
   OzArgs<double> z;
   z.p = p, z.As = (const uint32_t*)As, z.Bs = (const uint32_t*)Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np,
   z.Kp = Kp;
+  if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, double>(s, z, Np);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   static bool attr = false;
   if (!attr) {

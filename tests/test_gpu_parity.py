@@ -495,6 +495,28 @@ def test_mixed_kappa_sweep(kappa, method, dev, tc_handle):
     print(f"mixed kappa={kappa:g} {method}: rel.err(smallest)={abs(om[0] - om_r[0]) / om_r[0]:.2e}")
 
 
+@pytest.mark.parametrize("n", [1, 63, 130, 257])
+@pytest.mark.parametrize("method", METHODS)
+def test_mixed_tc_engines_agree(n, method, dev):
+    """The tcgen05 engine (TMEM accumulators, TMA staging; the default) and the
+    mma.sync engine compute the same exact FP32 level sums, so the two mixed
+    solves agree to rounding; every product goes through the tensor cores."""
+    A, B = _base(n, 900 + n)
+    outs = []
+    for engine in ("tcgen05", "mma_sync"):
+        h = bse.Handle()
+        h.set_tc_min_mnk(1)
+        h.set_tc_engine(engine)
+        outs.append(_gpu(A, B, method, dev, precision="mixed", handle=h))
+    (o1, X1, Y1), (o2, X2, Y2) = outs
+    assert np.max(np.abs(o1 - o2) / o2) <= 1e-13
+    a, b = phase_align(X1, Y1)
+    c, d = phase_align(X2, Y2)
+    tol = 1e-11 * o2.max() / _gaps(o2) + 1e-12
+    err = np.maximum(np.abs(a - c).max(axis=0), np.abs(b - d).max(axis=0))
+    assert np.all(err <= tol)
+
+
 def test_autotuner_batched_and_threshold(dev, tmp_path, monkeypatch):
     """The autotuner times both batched densities and the tensor-core thresholds,
     caches its choice, and the tuned settings give the same results."""
