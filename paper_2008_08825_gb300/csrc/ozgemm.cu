@@ -520,9 +520,10 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
   const uint32_t tmem = *tslot;
   volatile int* ab = abort_flag;
 
-  double acc64[UM_BN];
+  double acc64[UM_BN];  // units 2^-35 of the level-2 products
 #pragma unroll
   for (int q = 0; q < UM_BN; ++q) acc64[q] = 0.0;
+  uint64_t nanmask = 0;
 
   int issued = 0;  // producer: loads issued
   if (warp == 0 && lane == 0) {
@@ -579,6 +580,7 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
           }
         }
       }
+      if (!ok) break;
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty0 + 8 * st)
                    : "memory");
       if ((kt + 1) % OZ_FOLD == 0 || kt + 1 == ntile)
@@ -586,26 +588,38 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
                      : "memory");
     }
   } else if (warp >= 4) {
-    // folds: FP32 level sets -> FP64 registers
+    // folds.  Per column, the six level sums as exact integers in units of
+    // 2^-35 (levels 2..6 are exact FP32 integers in their own units 2^-7(l-2);
+    // the combined set of levels >= 7 rounds to the unit), combined exactly in
+    // int64 by Horner's rule, then one conversion and one FP64 add: 2 FP64
+    // operations per column and fold instead of 12.  A NaN or Inf level sum
+    // (non-finite input) marks its column, which ends as NaN.
     const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
     for (int f = 0; f < nfold; ++f) {
       if (!um_wait(tfull, f & 1, ab, ab)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-      for (int set = 0; set < OZ_NSETS; ++set) {
+      for (int c0 = 0; c0 < UM_BN; c0 += 8) {
+        int64_t tot[8];
 #pragma unroll
-        for (int c0 = 0; c0 < UM_BN; c0 += 16) {
-          uint32_t v[16];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];\n"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(tmem + lane_base + set * UM_BN + c0));
+        for (int set = 0; set < OZ_NSETS; ++set) {
+          uint32_t v[8];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                         "=r"(v[7])
+                       : "r"(tmem + lane_base + set * UM_BN + c0));
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          const float unit = set < OZ_NSETS - 1 ? (float)(1 << (7 * set)) : 34359738368.0f;  // 2^7s, 2^35
 #pragma unroll
-          for (int q = 0; q < 16; ++q) acc64[c0 + q] += (double)__uint_as_float(v[q]);
+          for (int q = 0; q < 8; ++q) {
+            const float x = __uint_as_float(v[q]);
+            if (set == 0 && !(fabsf(x) <= 3.0e38f)) nanmask |= 1ull << (c0 + q);
+            const int iv = __float2int_rn(x * unit);
+            tot[q] = set == 0 ? (int64_t)iv : tot[q] * 128 + iv;
+          }
         }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc64[c0 + q] += (double)tot[q];
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
@@ -652,10 +666,11 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
       const int fj = z.fb[j];
       double re = 0.0, im = 0.0;
       if (ei && fj) {
-        const int sc = (ei - 2048) + (fj - 2048) - 14;
+        const int sc = (ei - 2048) + (fj - 2048) - 14 - 35;
         re = ldexp(acc64[2 * jj], sc);
         im = ldexp(acc64[2 * jj + 1], sc);
       }
+      if ((nanmask >> (2 * jj)) & 3ull) re = im = __longlong_as_double(0x7ff8000000000000LL);
       cplx v = cmul(p.alpha, mkc(re, im));
       if (p.epi == EPI_XY) {
         const cplx v1 = p.P[i + j * p.ldp];
@@ -677,7 +692,8 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
       if (p.lowerC && i < j) break;
       const int fj = z.fb[j];
       double v = 0.0;
-      if (ei && fj) v = ldexp(acc64[jj], (ei - 2048) + (fj - 2048) - 14);
+      if (ei && fj) v = ldexp(acc64[jj], (ei - 2048) + (fj - 2048) - 14 - 35);
+      if ((nanmask >> jj) & 1ull) v = __longlong_as_double(0x7ff8000000000000LL);
       v *= p.alpha;
       if (use_beta) v += p.beta * p.C[i + j * p.ldc];
       p.C[i + j * p.ldc] = v;
