@@ -407,13 +407,22 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs<T> z) {
 //               slices of the B tile (S x 64 x 32), 64-byte swizzled;
 //   warp 1      MMA issuer (one thread): per stage and per 16-wide k step, the
 //               36 slice pairs t + u <= S + 1 as tcgen05.mma kind::f16
-//               (BF16 x BF16 -> FP32, M = 128, N = 64) into the TMEM
-//               accumulator of the pair's level set (6 sets x 64 columns);
+//               (BF16 x BF16 -> FP32, M = 128) into TMEM level sets of 64
+//               columns: sets 0..4 hold levels 2..6, sets 5 and 6 share the
+//               levels >= 7.  The pairs (t, u) and (t, u + 1) always land in
+//               adjacent sets, so they go as ONE N = 128 instruction whose B
+//               operand is the two consecutive B slices (16 N = 128 and 4
+//               N = 64 instructions per k step instead of 36 N = 64: an N = 64
+//               instruction costs ~55 cycles, an N = 128 one 64 cycles, the
+//               rate of the math);
 //   warp 2      allocates / frees the 512 TMEM columns;
-//   warps 4-7   every 512 k' (the exactness bound of the FP32 level sums) read
-//               the six sets (tcgen05.ld, one row per thread) and add them
-//               into FP64 registers; then the epilogue (scales, alpha/beta,
-//               the fused X/Y setup) straight from registers.
+//   warps 4-7   zero the sets first; every 512 k' (the exactness bound of the
+//               FP32 level sums) read the seven sets (tcgen05.ld, one row per
+//               thread), zero them again and add them into FP64 registers;
+//               then the epilogue (scales, alpha/beta, the fused X/Y setup)
+//               straight from registers.  Pre-zeroed sets let every MMA
+//               accumulate, so a paired instruction never mixes a fresh and
+//               a running set.
 // Two smem stages of 96 KB; mbarriers full/empty per stage and tmem_full /
 // tmem_empty per fold.  Every wait is bounded: on timeout the CTA records
 // BSE_ERR_TIMEOUT in the status word (when given), stops issuing, drains what
@@ -460,9 +469,11 @@ __device__ __forceinline__ uint64_t um_desc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
-// instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N, M
-constexpr uint32_t UM_IDESC =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_BN >> 3) << 17) | ((uint32_t)(UM_BM >> 4) << 24);
+// instruction descriptors: FP32 accumulate, BF16 A and B, both K-major, N, M
+__host__ __device__ constexpr uint32_t um_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM_BM >> 4) << 24);
+}
+constexpr int UM_NSETS = 7;  // levels 2..6, then two sets for the levels >= 7
 
 template <int S, typename T>
 __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, const __grid_constant__ CUtensorMap tmA,
@@ -520,10 +531,9 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
   const uint32_t tmem = *tslot;
   volatile int* ab = abort_flag;
 
-  double acc64[UM_BN];  // units 2^-35 of the level-2 products
+  double acc64[UM_BN];  // units 2^-28 of the level-2 products
 #pragma unroll
   for (int q = 0; q < UM_BN; ++q) acc64[q] = 0.0;
-  uint64_t nanmask = 0;
 
   int issued = 0;  // producer: loads issued
   if (warp == 0 && lane == 0) {
@@ -549,13 +559,11 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     bool ok = true;
-    uint32_t started = 0;  // bit s: set s written since the last fold
     for (int kt = 0; kt < ntile && ok; ++kt) {
       const int st = kt % UM_STAGES;
-      if (kt > 0 && kt % OZ_FOLD == 0) {
-        ok = um_wait(tempty, ((kt / OZ_FOLD) - 1) & 1, ab, ab);
+      if (kt % OZ_FOLD == 0) {  // the sets are zero (initially, or read and cleared by the last fold)
+        ok = um_wait(tempty, (kt / OZ_FOLD) & 1, ab, ab);
         if (!ok) break;
-        started = 0;
       }
       ok = um_wait(full0 + 8 * st, (kt / UM_STAGES) & 1, ab, ab);
       if (!ok) break;
@@ -567,16 +575,16 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
         for (int t = 0; t < S; ++t) {
           const uint64_t ad = um_desc(da + t * UM_SLICE_A + ks * 32);
 #pragma unroll
-          for (int u = 0; u < S - t; ++u) {
+          for (int u = 0; u < S - t; u += 2) {
+            // pair (t, u) [+ (t, u + 1)]: level t + u (0-based) -> column min(t + u, 5) * 64
             const int lev = t + u;
-            const int set = lev < OZ_NSETS - 1 ? lev : OZ_NSETS - 1;
+            const uint32_t col = (uint32_t)((lev < 5 ? lev : 5) * UM_BN);
             const uint64_t bd = um_desc(db + u * UM_SLICE_B + ks * 32);
-            const uint32_t accum = (started >> set) & 1u;
-            started |= 1u << set;
+            const uint32_t idesc = (u + 1 < S - t) ? um_idesc(2 * UM_BN) : um_idesc(UM_BN);
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + set * UM_BN),
-                "l"(ad), "l"(bd), "r"(UM_IDESC), "r"(accum));
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + col),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(1u));
           }
         }
       }
@@ -588,39 +596,61 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
                      : "memory");
     }
   } else if (warp >= 4) {
-    // folds.  Per column, the six level sums as exact integers in units of
-    // 2^-35 (levels 2..6 are exact FP32 integers in their own units 2^-7(l-2);
-    // the combined set of levels >= 7 rounds to the unit), combined exactly in
-    // int64 by Horner's rule, then one conversion and one FP64 add: 2 FP64
-    // operations per column and fold instead of 12.  A NaN or Inf level sum
-    // (non-finite input) marks its column, which ends as NaN.
+    // folds.  Per column, levels 2..6 are exact FP32 integers in their own
+    // units 2^-7(l-2); combined by Horner's rule in int64, in units of 2^-28,
+    // their sum stays below 2^53, so it converts to FP64 exactly.  The two
+    // sets of levels >= 7 (FP32-rounded, like any FP32 accumulation) are
+    // added in FP32 and then in FP64.  4 FP64 operations per column and fold
+    // instead of 14; a non-finite input reaches the result through the
+    // levels >= 7 (every slice of a non-finite entry is NaN).
     const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+    const uint32_t z = 0;
+    auto clear_sets = [&](int c0) {
+#pragma unroll
+      for (int set = 0; set < UM_NSETS; ++set)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(
+                         tmem + lane_base + set * UM_BN + c0),
+                     "r"(z));
+    };
+    if (nfold > 0) {
+#pragma unroll
+      for (int c0 = 0; c0 < UM_BN; c0 += 8) clear_sets(c0);
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty) : "memory");
+    }
     for (int f = 0; f < nfold; ++f) {
       if (!um_wait(tfull, f & 1, ab, ab)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int c0 = 0; c0 < UM_BN; c0 += 8) {
         int64_t tot[8];
+        float low[8];
 #pragma unroll
-        for (int set = 0; set < OZ_NSETS; ++set) {
+        for (int set = 0; set < UM_NSETS; ++set) {
           uint32_t v[8];
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                          "=r"(v[7])
                        : "r"(tmem + lane_base + set * UM_BN + c0));
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-          const float unit = set < OZ_NSETS - 1 ? (float)(1 << (7 * set)) : 34359738368.0f;  // 2^7s, 2^35
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float x = __uint_as_float(v[q]);
-            if (set == 0 && !(fabsf(x) <= 3.0e38f)) nanmask |= 1ull << (c0 + q);
-            const int iv = __float2int_rn(x * unit);
-            tot[q] = set == 0 ? (int64_t)iv : tot[q] * 128 + iv;
+            if (set < 5) {
+              const int iv = __float2int_rn(x * (float)(1 << (7 * set)));  // exact
+              tot[q] = set == 0 ? (int64_t)iv : tot[q] * 128 + iv;
+            } else {
+              low[q] = set == 5 ? x : low[q] + x;
+            }
           }
         }
+        if (f + 1 < nfold) clear_sets(c0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc64[c0 + q] += (double)tot[q];
+        for (int q = 0; q < 8; ++q) acc64[c0 + q] = fma((double)low[q], 268435456.0, acc64[c0 + q] + (double)tot[q]);
       }
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty) : "memory");
@@ -666,11 +696,10 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
       const int fj = z.fb[j];
       double re = 0.0, im = 0.0;
       if (ei && fj) {
-        const int sc = (ei - 2048) + (fj - 2048) - 14 - 35;
+        const int sc = (ei - 2048) + (fj - 2048) - 14 - 28;
         re = ldexp(acc64[2 * jj], sc);
         im = ldexp(acc64[2 * jj + 1], sc);
       }
-      if ((nanmask >> (2 * jj)) & 3ull) re = im = __longlong_as_double(0x7ff8000000000000LL);
       cplx v = cmul(p.alpha, mkc(re, im));
       if (p.epi == EPI_XY) {
         const cplx v1 = p.P[i + j * p.ldp];
@@ -692,8 +721,7 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
       if (p.lowerC && i < j) break;
       const int fj = z.fb[j];
       double v = 0.0;
-      if (ei && fj) v = ldexp(acc64[jj], (ei - 2048) + (fj - 2048) - 14 - 35);
-      if ((nanmask >> jj) & 1ull) v = __longlong_as_double(0x7ff8000000000000LL);
+      if (ei && fj) v = ldexp(acc64[jj], (ei - 2048) + (fj - 2048) - 14 - 28);
       v *= p.alpha;
       if (use_beta) v += p.beta * p.C[i + j * p.ldc];
       p.C[i + j * p.ldc] = v;
