@@ -489,24 +489,24 @@ def main():
         el_m, l_m, pr_m, ck_m, om_m = results["mixed"]
         bf16_sustained = measured_peaks().get("bf16_tflops_sustained", 1700.0)
         diff = max(float(np.max(np.abs(a - b) / b)) for a, b in zip(om_m, om_head))
-        mma_flops = pr_m["gemm_flops"] * 36.0  # 36 BF16 slice products per FP64-equivalent product
+        tc_bf16 = pr_m["tc_flops"] * 36.0  # 36 BF16 slice-pair products per FP64-equivalent product
+        tc_rate = tc_bf16 / (pr_m["tc_ms"] / 1e3) / 1e12 if pr_m["tc_ms"] > 0 else None
         line["mixed"] = {
             "value": len(methods) * args.steps * world / el_m, "unit": "solves/s", "ms_per_step": el_m / args.steps * 1e3,
             "speedup_vs_fp64": elapsed / el_m, "model_tflops": model * args.steps * world / el_m / 1e12,
             "max_rel_diff_omega_vs_fp64": diff, "gpu_launches": l_m, "clocks": ck_m,
             "stage_ms_per_step": {k: v / args.steps for k, v in zip(stage_names, pr_m["stage_ms"]) if v > 0},
-            "roofline": {"bound": "tensor", "kernel": "oz_umma_kernel<8> (tcgen05.mma BF16 -> FP32 TMEM, TMA-staged "
-                                                  "split FP64 operands)",
-                         "achieved": mma_flops / (pr_m["gemm_ms"] / 1e3) / 1e12 if pr_m["gemm_ms"] > 0 else None,
-                         "peak": bf16_sustained, "unit": "TFLOP/s",
-                         "frac": (mma_flops / (pr_m["gemm_ms"] / 1e3) / 1e12 / bf16_sustained)
-                         if pr_m["gemm_ms"] > 0 else None,
-                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (products timed inside a long "
-                                        "step); achieved counts the 36 "
-                                        "BF16 slice products per FP64-equivalent product over all product launches "
-                                        "(split kernels and the DFMA engine's small products included in the time)",
-                         "fp64_equivalent_tflops": pr_m["gemm_flops"] / (pr_m["gemm_ms"] / 1e3) / 1e12
-                         if pr_m["gemm_ms"] > 0 else None,
+            "roofline": {"bound": "tensor",
+                         "kernel": "oz_umma_kernel<8> (tcgen05.mma BF16 -> FP32 TMEM, TMA-staged split FP64 operands)",
+                         "achieved": tc_rate, "peak": bf16_sustained, "unit": "TFLOP/s",
+                         "frac": tc_rate / bf16_sustained if tc_rate else None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                         "what": "36 BF16 slice-pair products per FP64-equivalent useful flop, over the summed "
+                                 "CUDA-event durations of the product kernel's launches (operand splitting excluded)",
+                         "kernel_ms_per_step": pr_m["tc_ms"] / args.steps, "launches_per_step": pr_m["tc_launches"] / args.steps,
+                         "fp64_equivalent_tflops": pr_m["tc_flops"] / (pr_m["tc_ms"] / 1e3) / 1e12 if pr_m["tc_ms"] > 0 else None,
+                         "products_incl_splitting_fp64_equivalent_tflops":
+                             pr_m["gemm_flops"] / (pr_m["gemm_ms"] / 1e3) / 1e12 if pr_m["gemm_ms"] > 0 else None,
                          "traffic": None},
         }
     print(json.dumps(line), flush=True)
@@ -518,14 +518,16 @@ def _read_profile(bse, h):
     class PD(ctypes.Structure):
         _fields_ = [("stage_ms", ctypes.c_double * 10), ("stage_calls", ctypes.c_int64 * 10),
                     ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double), ("gemm_launches", ctypes.c_int64),
-                    ("launches", ctypes.c_int64)]
+                    ("launches", ctypes.c_int64), ("tc_ms", ctypes.c_double), ("tc_flops", ctypes.c_double),
+                    ("tc_launches", ctypes.c_int64)]
 
     pd = PD()
     L = bse.lib()
     L.bse_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(PD)]
     bse._check(L.bse_profile_read(h.ptr, ctypes.byref(pd)))
     return {"stage_ms": list(pd.stage_ms), "gemm_ms": pd.gemm_ms, "gemm_flops": pd.gemm_flops,
-            "gemm_launches": pd.gemm_launches, "launches": pd.launches}
+            "gemm_launches": pd.gemm_launches, "launches": pd.launches, "tc_ms": pd.tc_ms, "tc_flops": pd.tc_flops,
+            "tc_launches": pd.tc_launches}
 
 
 if __name__ == "__main__":

@@ -275,6 +275,12 @@ typedef struct bse_profile_data {
   double gemm_flops;      /* useful flops of those launches */
   int64_t gemm_launches;
   int64_t launches;       /* all kernel launches while enabled */
+  /* mixed form: the tensor-core product kernels alone (operand splitting
+   * excluded), with the FP64-equivalent useful flops of their products;
+   * one BF16 slice-pair product set is 36 times those flops */
+  double tc_ms;
+  double tc_flops;
+  int64_t tc_launches;
 } bse_profile_data;
 /* enable: 0 off, 1 stages and GEMMs, 2 additionally every launch of the
  * reduction and tridiagonal kernels (adds two events per launch). */

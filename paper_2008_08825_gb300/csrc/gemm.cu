@@ -90,8 +90,9 @@ bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
   if (oz.ptr && p.opA != OPT && p.opB != OPT && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
     const bool prof = prof_current() != nullptr;
     if (prof) prof_gemm_begin(s);
-    const bse_status r = gemm_z_oz_raw(s, p);
-    if (prof) prof_gemm_end(s, useful_macs(p) * 8.0);
+    const double flops = useful_macs(p) * 8.0;
+    const bse_status r = gemm_z_oz_raw(s, p, flops);
+    if (prof) prof_gemm_end(s, flops);
     return r;
   }
   return gemm_launch<cplx, 8>(s, p);
@@ -101,8 +102,9 @@ bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) {
   if (oz.ptr && p.opA != OPC && p.opB != OPC && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
     const bool prof = prof_current() != nullptr;
     if (prof) prof_gemm_begin(s);
-    const bse_status r = gemm_d_oz_raw(s, p);
-    if (prof) prof_gemm_end(s, useful_macs(p) * 2.0);
+    const double flops = useful_macs(p) * 2.0;
+    const bse_status r = gemm_d_oz_raw(s, p, flops);
+    if (prof) prof_gemm_end(s, flops);
     return r;
   }
   return gemm_launch<double, 16>(s, p);

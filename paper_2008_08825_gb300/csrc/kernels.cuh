@@ -142,5 +142,6 @@ struct OzWork {
 void oz_set_current(const OzWork& w);
 OzWork oz_current();
 size_t oz_work_bytes(int64_t maxdim, int slices);
-bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p);
-bse_status gemm_d_oz_raw(cudaStream_t s, const GemmParams<double>& p);
+// fp64_flops: the product's useful FP64-equivalent flops (for the profiler)
+bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p, double fp64_flops);
+bse_status gemm_d_oz_raw(cudaStream_t s, const GemmParams<double>& p, double fp64_flops);

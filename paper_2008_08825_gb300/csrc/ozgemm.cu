@@ -416,13 +416,13 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs<T> z) {
 //               instruction costs ~55 cycles, an N = 128 one 64 cycles, the
 //               rate of the math);
 //   warp 2      allocates / frees the 512 TMEM columns;
-//   warps 4-7   zero the sets first; every 512 k' (the exactness bound of the
-//               FP32 level sums) read the seven sets (tcgen05.ld, one row per
-//               thread), zero them again and add them into FP64 registers;
-//               then the epilogue (scales, alpha/beta, the fused X/Y setup)
-//               straight from registers.  Pre-zeroed sets let every MMA
-//               accumulate, so a paired instruction never mixes a fresh and
-//               a running set.
+//   warps 4-11  zero the sets first; every 512 k' (the exactness bound of the
+//               FP32 level sums) read the seven sets (tcgen05.ld; a thread
+//               owns one row and 32 of the 64 columns), zero them again and
+//               add them into int64 registers; then the epilogue (scales,
+//               alpha/beta, the fused X/Y setup) straight from registers.
+//               Pre-zeroed sets let every MMA accumulate, so a paired
+//               instruction never mixes a fresh and a running set.
 // Two smem stages of 96 KB; mbarriers full/empty per stage and tmem_full /
 // tmem_empty per fold.  Every wait is bounded: on timeout the CTA records
 // BSE_ERR_TIMEOUT in the status word (when given), stops issuing, drains what
@@ -476,7 +476,7 @@ __host__ __device__ constexpr uint32_t um_idesc(int n) {
 constexpr int UM_NSETS = 7;  // levels 2..6, then two sets for the levels >= 7
 
 template <int S, typename T>
-__global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ __align__(1024) unsigned char usm[];
   using L = UmLayout<S>;
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty0 + 8 * q));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(tempty));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(tempty));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(drain));
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -531,9 +531,15 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
   const uint32_t tmem = *tslot;
   volatile int* ab = abort_flag;
 
-  double acc64[UM_BN];  // units 2^-28 of the level-2 products
+  constexpr int EC = UM_BN / 2;  // columns per epilogue thread
+  // a column's value = hi 2^-28 + lo 2^-45 in units of the level-2 products;
+  // after each fold lo keeps only the remainder 0 <= lo < 2^17 (its multiples
+  // of 2^17 move into hi exactly), so it stays a 32-bit integer
+  int64_t hi[EC];
+  int32_t lo[EC];
 #pragma unroll
-  for (int q = 0; q < UM_BN; ++q) acc64[q] = 0.0;
+  for (int q = 0; q < EC; ++q) hi[q] = 0, lo[q] = 0;
+  uint32_t nanmask = 0;
 
   int issued = 0;  // producer: loads issued
   if (warp == 0 && lane == 0) {
@@ -596,25 +602,26 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
                      : "memory");
     }
   } else if (warp >= 4) {
-    // folds.  Per column, levels 2..6 are exact FP32 integers in their own
-    // units 2^-7(l-2); combined by Horner's rule in int64, in units of 2^-28,
-    // their sum stays below 2^53, so it converts to FP64 exactly.  The two
-    // sets of levels >= 7 (FP32-rounded, like any FP32 accumulation) are
-    // added in FP32 and then in FP64.  4 FP64 operations per column and fold
-    // instead of 14; a non-finite input reaches the result through the
-    // levels >= 7 (every slice of a non-finite entry is NaN).
-    const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+    // folds, all in integers: per column, levels 2..6 are exact FP32
+    // integers in their own units 2^-7(l-2) and combine exactly by Horner's
+    // rule into units of 2^-28 (below 2^52 per fold); the two sets of levels
+    // >= 7 round to units of 2^-45, i.e. 2^-59 of the largest product (an
+    // integer part at 2^-38 plus the rounded remainder, below 2^35 per fold).
+    // No FP64 work until the epilogue.  A non-finite level sum (non-finite
+    // input) marks its column, which ends as NaN.
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int col0 = ((warp - 4) >> 2) * EC;
     const uint32_t z = 0;
     auto clear_sets = [&](int c0) {
 #pragma unroll
       for (int set = 0; set < UM_NSETS; ++set)
         asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(
-                         tmem + lane_base + set * UM_BN + c0),
+                         tmem + lane_base + set * UM_BN + col0 + c0),
                      "r"(z));
     };
     if (nfold > 0) {
 #pragma unroll
-      for (int c0 = 0; c0 < UM_BN; c0 += 8) clear_sets(c0);
+      for (int c0 = 0; c0 < EC; c0 += 8) clear_sets(c0);
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
@@ -624,31 +631,37 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
       if (!um_wait(tfull, f & 1, ab, ab)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-      for (int c0 = 0; c0 < UM_BN; c0 += 8) {
-        int64_t tot[8];
-        float low[8];
+      for (int c0 = 0; c0 < EC; c0 += 4) {
+        int64_t tot[4], low[4];
 #pragma unroll
         for (int set = 0; set < UM_NSETS; ++set) {
-          uint32_t v[8];
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                         "=r"(v[7])
-                       : "r"(tmem + lane_base + set * UM_BN + c0));
+          uint32_t v[4];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                       : "r"(tmem + lane_base + set * UM_BN + col0 + c0));
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 4; ++q) {
             const float x = __uint_as_float(v[q]);
             if (set < 5) {
               const int iv = __float2int_rn(x * (float)(1 << (7 * set)));  // exact
               tot[q] = set == 0 ? (int64_t)iv : tot[q] * 128 + iv;
             } else {
-              low[q] = set == 5 ? x : low[q] + x;
+              if (!(fabsf(x) <= 3.0e38f)) nanmask |= 1u << (c0 + q);
+              const float y = x * 274877906944.0f;  // 2^38, exact
+              const float yi = rintf(y);
+              const int64_t iv = (int64_t)(int)yi * 128 + __float2int_rn((y - yi) * 128.0f);  // units 2^-45
+              low[q] = set == 5 ? iv : low[q] + iv;
             }
           }
         }
-        if (f + 1 < nfold) clear_sets(c0);
+        if (f + 1 < nfold && (c0 & 7) == 4) clear_sets(c0 - 4);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc64[c0 + q] = fma((double)low[q], 268435456.0, acc64[c0 + q] + (double)tot[q]);
+        for (int q = 0; q < 4; ++q) {
+          const int64_t l = (int64_t)lo[c0 + q] + low[q];
+          hi[c0 + q] += tot[q] + (l >> 17);
+          lo[c0 + q] = (int32_t)(l & 0x1FFFF);
+        }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -681,24 +694,31 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
     return;
   }
   if (warp < 4) return;
-  // epilogue: thread = one row of the tile; complex -- real columns (2j, 2j+1)
-  // are (Re, Im) of logical column jc0 + j; real -- column jc0 + q
-  const int64_t i = i0 + (warp - 4) * 32 + lane;
+  // epilogue: thread = one row of the tile and columns [col0, col0 + 32) of
+  // its 64 real columns; complex -- real columns (2j, 2j+1) are (Re, Im) of
+  // logical column jc0 + col0/2 + j; real -- column jc0 + col0 + q
+  const int64_t i = i0 + (warp & 3) * 32 + lane;
   if (i >= p.m) return;
+  const int col0 = ((warp - 4) >> 2) * EC;
   const int ei = z.ea[i];
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  auto value = [&](int q, int sc) -> double {
+    if ((nanmask >> q) & 1u) return qnan;
+    return ldexp((double)hi[q], sc - 28) + ldexp((double)lo[q], sc - 45);
+  };
   if constexpr (CPLX) {
     const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
 #pragma unroll
-    for (int jj = 0; jj < UM_BN / 2; ++jj) {
-      const int64_t j = jc0 + jj;
+    for (int jj = 0; jj < EC / 2; ++jj) {
+      const int64_t j = jc0 + col0 / 2 + jj;
       if (j >= p.n) break;
       if (p.lowerC && i < j) break;
       const int fj = z.fb[j];
       double re = 0.0, im = 0.0;
       if (ei && fj) {
-        const int sc = (ei - 2048) + (fj - 2048) - 14 - 28;
-        re = ldexp(acc64[2 * jj], sc);
-        im = ldexp(acc64[2 * jj + 1], sc);
+        const int sc = (ei - 2048) + (fj - 2048) - 14;
+        re = value(2 * jj, sc);
+        im = value(2 * jj + 1, sc);
       }
       cplx v = cmul(p.alpha, mkc(re, im));
       if (p.epi == EPI_XY) {
@@ -715,13 +735,13 @@ __global__ void __launch_bounds__(256, 1) oz_umma_kernel(const OzArgs<T> z, cons
   } else {
     const bool use_beta = p.beta != 0.0;
 #pragma unroll
-    for (int jj = 0; jj < UM_BN; ++jj) {
-      const int64_t j = jc0 + jj;
+    for (int jj = 0; jj < EC; ++jj) {
+      const int64_t j = jc0 + col0 + jj;
       if (j >= p.n) break;
       if (p.lowerC && i < j) break;
       const int fj = z.fb[j];
       double v = 0.0;
-      if (ei && fj) v = ldexp(acc64[jj], (ei - 2048) + (fj - 2048) - 14 - 28);
+      if (ei && fj) v = value(jj, (ei - 2048) + (fj - 2048) - 14);
       v *= p.alpha;
       if (use_beta) v += p.beta * p.C[i + j * p.ldc];
       p.C[i + j * p.ldc] = v;
@@ -850,7 +870,7 @@ static bool slice_map(CUtensorMap* m, const void* base, int S, int64_t rows, int
 }
 
 template <int S, typename T>
-static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_real) {
+static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_real, double flops) {
   CUtensorMap ta, tb;
   if (!slice_map(&ta, z.As, S, z.Mp, z.Kp, UM_BM) || !slice_map(&tb, z.Bs, S, z.Np, z.Kp, UM_BN)) {
     bse_internal_set_error("tensor-core GEMM: cuTensorMapEncodeTiled failed");
@@ -863,14 +883,16 @@ static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_
     attr = true;
   }
   dim3 grid((unsigned)((ncols_real + UM_BN - 1) / UM_BN), (unsigned)((z.Mp + UM_BM - 1) / UM_BM));
-  oz_umma_kernel<S, T><<<grid, 256, UmLayout<S>::SMEM, s>>>(z, ta, tb);
+  prof_tc_begin(s);
+  oz_umma_kernel<S, T><<<grid, 384, UmLayout<S>::SMEM, s>>>(z, ta, tb);
+  prof_tc_end(s, flops);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
 
 template <int S>
-static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p) {
+static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p, double flops) {
   const int64_t Mp = (p.m + OZ_BM - 1) / OZ_BM * OZ_BM;
   const int64_t Np = (2 * p.n + OZ_BN - 1) / OZ_BN * OZ_BN;
   const int64_t Kp = (2 * p.k + OZ_BK - 1) / OZ_BK * OZ_BK;
@@ -896,7 +918,7 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p) {
   BSE_LAUNCH_CHECK();
   OzArgs<cplx> z;
   z.p = p, z.As = As, z.Bs = Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np, z.Kp = Kp;
-  if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, cplx>(s, z, Np);
+  if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, cplx>(s, z, Np, flops);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   static bool attr = false;
   if (!attr) {
@@ -904,23 +926,25 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p) {
     attr = true;
   }
   dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
+  prof_tc_begin(s);
   oz_mma_kernel<S, cplx><<<grid, 256, smem, s>>>(z);
+  prof_tc_end(s, flops);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
 
-bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p) {
+bse_status gemm_z_oz_raw(cudaStream_t s, const GemmParams<cplx>& p, double fp64_flops) {
   if (p.m <= 0 || p.n <= 0) return BSE_OK;
   if (p.opA == OPT || p.opB == OPT) {
     bse_internal_set_error("tensor-core GEMM: transpose without conjugate is not supported");
     return BSE_ERR_ARG;
   }
-  return oz_run<8>(s, p);
+  return oz_run<8>(s, p, fp64_flops);
 }
 
 template <int S>
-static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p) {
+static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p, double flops) {
   const int64_t Mp = (p.m + OZ_BM - 1) / OZ_BM * OZ_BM;
   const int64_t Np = (p.n + OZ_BN - 1) / OZ_BN * OZ_BN;
   const int64_t Kp = (p.k + OZ_BK - 1) / OZ_BK * OZ_BK;
@@ -947,7 +971,7 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p) {
   OzArgs<double> z;
   z.p = p, z.As = (const uint32_t*)As, z.Bs = (const uint32_t*)Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np,
   z.Kp = Kp;
-  if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, double>(s, z, Np);
+  if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, double>(s, z, Np, flops);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   static bool attr = false;
   if (!attr) {
@@ -955,17 +979,19 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p) {
     attr = true;
   }
   dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
+  prof_tc_begin(s);
   oz_mma_kernel<S, double><<<grid, 256, smem, s>>>(z);
+  prof_tc_end(s, flops);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
 
-bse_status gemm_d_oz_raw(cudaStream_t s, const GemmParams<double>& p) {
+bse_status gemm_d_oz_raw(cudaStream_t s, const GemmParams<double>& p, double fp64_flops) {
   if (p.m <= 0 || p.n <= 0) return BSE_OK;
   if (p.opA == OPC || p.opB == OPC) {
     bse_internal_set_error("tensor-core real GEMM: conjugate transpose is not meaningful");
     return BSE_ERR_ARG;
   }
-  return oz_run_d<8>(s, p);
+  return oz_run_d<8>(s, p, fp64_flops);
 }

@@ -13,7 +13,7 @@ long long bse_total_launches();
 struct Profiler {
   std::vector<cudaEvent_t> pool;
   struct Rec {
-    int kind;  // 0 stage, 1 gemm, 2 named launch
+    int kind;  // 0 stage, 1 gemm, 2 named launch, 3 tensor-core product kernel
     int stage;
     double flops;
     cudaEvent_t a, b;
@@ -27,6 +27,7 @@ struct Profiler {
   bse_profile_data acc;
   long long launches0 = 0;
   cudaEvent_t gemm_a = nullptr;
+  cudaEvent_t tc_a = nullptr;
 
   cudaEvent_t get() {
     if (!pool.empty()) {
@@ -101,6 +102,22 @@ void prof_gemm_end(cudaStream_t s, double flops) {
   p->done.push_back(r);
 }
 
+void prof_tc_begin(cudaStream_t s) {
+  Profiler* p = g_cur;
+  if (!p) return;
+  p->tc_a = p->get();
+  if (p->tc_a) cudaEventRecord(p->tc_a, s);
+}
+
+void prof_tc_end(cudaStream_t s, double flops) {
+  Profiler* p = g_cur;
+  if (!p || !p->tc_a) return;
+  Profiler::Rec r{3, 0, flops, p->tc_a, p->get(), nullptr};
+  if (r.b) cudaEventRecord(r.b, s);
+  p->tc_a = nullptr;
+  p->done.push_back(r);
+}
+
 bool prof_fine() { return g_cur && g_cur->fine; }
 void prof_set_fine(Profiler* p, int fine) { p->fine = fine; }
 
@@ -147,6 +164,10 @@ void prof_flush(Profiler* p) {
       } else if (r.kind == 0) {
         p->acc.stage_ms[r.stage] += ms;
         p->acc.stage_calls[r.stage] += 1;
+      } else if (r.kind == 3) {
+        p->acc.tc_ms += ms;
+        p->acc.tc_flops += r.flops;
+        p->acc.tc_launches += 1;
       } else {
         p->acc.gemm_ms += ms;
         p->acc.gemm_flops += r.flops;

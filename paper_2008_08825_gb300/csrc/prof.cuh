@@ -16,6 +16,9 @@ void prof_stage_begin(int stage, cudaStream_t s);
 void prof_stage_end(int stage, cudaStream_t s);
 void prof_gemm_begin(cudaStream_t s);
 void prof_gemm_end(cudaStream_t s, double flops);
+// the tensor-core product kernel inside a split-operand product
+void prof_tc_begin(cudaStream_t s);
+void prof_tc_end(cudaStream_t s, double flops);
 // fine level: every wrapped launch timed and accumulated under its name
 bool prof_fine();
 void prof_launch_begin(cudaStream_t s);
