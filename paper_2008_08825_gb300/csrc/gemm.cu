@@ -78,7 +78,9 @@ static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
   }
   const bool prof = prof_current() != nullptr;
   if (prof) prof_gemm_begin(s);
+  prof_launch_begin(s);
   gemm_kernel<T, BK><<<grid, 256, 0, s>>>(p);
+  prof_launch_end(s, sizeof(T) == sizeof(cplx) ? "gemm_kernel<cplx> (DFMA)" : "gemm_kernel<real>");
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   if (prof) prof_gemm_end(s, sizeof(T) == sizeof(float) ? 0.0 : useful_macs(p) * (sizeof(T) == sizeof(cplx) ? 8.0 : 2.0));

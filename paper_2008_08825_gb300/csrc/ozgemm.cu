@@ -40,13 +40,42 @@ __device__ __forceinline__ uint16_t bf16_bits_exact(float v) {
   return (uint16_t)(__float_as_uint(v) >> 16);
 }
 
+// Slices of v (|v| < 2^e): v 2^(7 - e) = sum_t q_t 2^(-7(t-1)) with integers
+// |q_1| <= 128, |q_t| <= 64 (t >= 2), each digit rounded to nearest in turn
+// and the tail below the last digit rounded, returned as the exact FP32 (and
+// BF16) numbers q_t 2^(-7(t-1)).  Integer arithmetic on the bit pattern only:
+// FP64 is the slowest unit of this part.  A NaN or Inf entry gives NaN slices.
 __device__ __forceinline__ void split_value(double v, int e, int S, float* out) {
-  double r = ldexp(v, 7 - e);  // |r| < 128
-  for (int t = 0; t < S; ++t) {
-    const double q = rint(r);
-    out[t] = (float)ldexp(q, -7 * t);
-    r = (r - q) * 128.0;
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  if (ef == 0x7FF) {
+    for (int t = 0; t < S; ++t) out[t] = __int_as_float(0x7FC00000);
+    return;
   }
+  uint64_t M = b & 0xFFFFFFFFFFFFFull;  // v = +-M 2^E
+  const int E = ef ? ef - 1075 : -1074;
+  if (ef) M |= 1ull << 52;
+  // R = round(|v| 2^(7S - e)): the digits' common integer scale; sh <= 7S - 53
+  // because M < 2^53 and M 2^E < 2^e
+  const int sh = E + 7 * S - e;
+  int64_t R = 0;
+  if (M && sh > -64) R = sh >= 0 ? (int64_t)(M << sh) : (int64_t)((M + (1ull << (-sh - 1))) >> (-sh));
+  if (b >> 63) R = -R;
+  for (int t = 0; t < S - 1; ++t) {
+    const int sd = 7 * (S - 1 - t);
+    const int64_t q = (R + (1ll << (sd - 1))) >> sd;  // nearest (ties up)
+    R -= q * (1ll << sd);
+    out[t] = (float)(int)q * __int_as_float((127 - 7 * t) << 23);
+  }
+  out[S - 1] = (float)(int)R * __int_as_float((127 - 7 * (S - 1)) << 23);
+}
+
+// frexp exponent of x (|x| = m 2^e, 1/2 <= m < 1) from its bit pattern; -4096 for 0
+__device__ __forceinline__ int fexp_bits(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return -4096;
+  const int ef = (int)(b >> 52);
+  return ef ? ef - 1022 : -1010 - __clzll((long long)b);
 }
 
 // ---- scales -----------------------------------------------------------------
@@ -66,7 +95,7 @@ __device__ __forceinline__ bool op_elem(const cplx* X, int64_t ldx, int op, int 
 // rows of op(A) (m x k): one warp per row chunk; atomicMax on biased exponents
 __global__ void oz_rowexp_kernel(int64_t m, int64_t k, const cplx* A, int64_t lda, int op, int tri, int* ea) {
   // tile of 32 rows x 32 columns, coalesced along the stored leading dimension
-  __shared__ double mx[32][33];
+  __shared__ int mx[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int q = ty; q < 32; q += 8) {
@@ -74,24 +103,20 @@ __global__ void oz_rowexp_kernel(int64_t m, int64_t k, const cplx* A, int64_t ld
     if (op == OPN) r = r0 + tx, c = c0 + q;  // consecutive tx -> consecutive rows (stored contiguous)
     else r = r0 + q, c = c0 + tx;
     cplx v;
-    double a = 0.0;
-    if (op_elem(A, lda, op, tri, r, c, m, k, &v)) a = fmax(fabs(v.x), fabs(v.y));
+    int a = -4096;
+    if (op_elem(A, lda, op, tri, r, c, m, k, &v)) a = max(fexp_bits(v.x), fexp_bits(v.y));
     if (op == OPN) mx[tx][q] = a; else mx[q][tx] = a;
   }
   __syncthreads();
   if (ty == 0) {
-    double a = 0.0;
-    for (int q = 0; q < 32; ++q) a = fmax(a, mx[tx][q]);
-    if (a > 0.0 && r0 + tx < m) {
-      int e;
-      frexp(a, &e);
-      atomicMax(ea + r0 + tx, 2048 + e);
-    }
+    int a = -4096;
+    for (int q = 0; q < 32; ++q) a = max(a, mx[tx][q]);
+    if (a > -4096 && r0 + tx < m) atomicMax(ea + r0 + tx, 2048 + a);
   }
 }
 
 __global__ void oz_colexp_kernel(int64_t k, int64_t n, const cplx* B, int64_t ldb, int op, int tri, int* fb) {
-  __shared__ double mx[32][33];
+  __shared__ int mx[32][33];
   const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;  // c: column j of op(B), r: kk
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int q = ty; q < 32; q += 8) {
@@ -99,19 +124,15 @@ __global__ void oz_colexp_kernel(int64_t k, int64_t n, const cplx* B, int64_t ld
     if (op == OPN) r = r0 + tx, c = c0 + q;  // op(B) = B: rows kk contiguous
     else r = r0 + q, c = c0 + tx;
     cplx v;
-    double a = 0.0;
-    if (op_elem(B, ldb, op, tri, r, c, k, n, &v)) a = fmax(fabs(v.x), fabs(v.y));
+    int a = -4096;
+    if (op_elem(B, ldb, op, tri, r, c, k, n, &v)) a = max(fexp_bits(v.x), fexp_bits(v.y));
     if (op == OPN) mx[q][tx] = a; else mx[tx][q] = a;  // mx[col][row]
   }
   __syncthreads();
   if (ty == 0) {
-    double a = 0.0;
-    for (int q = 0; q < 32; ++q) a = fmax(a, mx[tx][q]);
-    if (a > 0.0 && c0 + tx < n) {
-      int e;
-      frexp(a, &e);
-      atomicMax(fb + c0 + tx, 2048 + e);
-    }
+    int a = -4096;
+    for (int q = 0; q < 32; ++q) a = max(a, mx[tx][q]);
+    if (a > -4096 && c0 + tx < n) atomicMax(fb + c0 + tx, 2048 + a);
   }
 }
 
@@ -762,28 +783,25 @@ __device__ __forceinline__ bool op_elem_d(const double* X, int64_t ldx, int op, 
 // exponents of rows (rowsx = 1) of op(A) or of columns (rowsx = 0) of op(B)
 __global__ void oz_exp_d_kernel(int64_t R, int64_t C, const double* X, int64_t ldx, int op, int tri, int rowsx,
                                 int* ex) {
-  __shared__ double mx[32][33];
+  __shared__ int mx[32][33];
   const int64_t b0 = (int64_t)blockIdx.y * 32, b1 = (int64_t)blockIdx.x * 32;  // (row block, col block)
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int q = ty; q < 32; q += 8) {
     int64_t r, c;
     if (op == OPN) r = b0 + tx, c = b1 + q;
     else r = b0 + q, c = b1 + tx;
-    double v = 0.0, a = 0.0;
-    if (op_elem_d(X, ldx, op, tri, r, c, R, C, &v)) a = fabs(v);
+    double v = 0.0;
+    int a = -4096;
+    if (op_elem_d(X, ldx, op, tri, r, c, R, C, &v)) a = fexp_bits(v);
     const int lr = (int)(r - b0), lc = (int)(c - b1);
     if (rowsx) mx[lr][lc] = a; else mx[lc][lr] = a;
   }
   __syncthreads();
   if (ty == 0) {
-    double a = 0.0;
-    for (int q = 0; q < 32; ++q) a = fmax(a, mx[tx][q]);
+    int a = -4096;
+    for (int q = 0; q < 32; ++q) a = max(a, mx[tx][q]);
     const int64_t idx = (rowsx ? b0 : b1) + tx;
-    if (a > 0.0 && idx < (rowsx ? R : C)) {
-      int e;
-      frexp(a, &e);
-      atomicMax(ex + idx, 2048 + e);
-    }
+    if (a > -4096 && idx < (rowsx ? R : C)) atomicMax(ex + idx, 2048 + a);
   }
 }
 
@@ -884,7 +902,9 @@ static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_
   }
   dim3 grid((unsigned)((ncols_real + UM_BN - 1) / UM_BN), (unsigned)((z.Mp + UM_BM - 1) / UM_BM));
   prof_tc_begin(s);
+  prof_launch_begin(s);
   oz_umma_kernel<S, T><<<grid, 384, UmLayout<S>::SMEM, s>>>(z, ta, tb);
+  prof_launch_end(s, "oz_umma_kernel");
   prof_tc_end(s, flops);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
@@ -906,6 +926,7 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p, double flops
   uint32_t* Bs = (uint32_t*)(base + (size_t)S * Mp * Kp * 2);
   int* ea = (int*)(base + (size_t)S * (Mp + Np) * Kp * 2);
   int* fb = ea + Mp;
+  prof_launch_begin(s);
   BSE_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (Mp + Np / 2), s));
   dim3 tb(32, 8);
   oz_rowexp_kernel<<<dim3(ceil_div_u(p.k, 32), ceil_div_u(p.m, 32)), tb, 0, s>>>(p.m, p.k, p.A, p.lda, p.opA, p.triA, ea);
@@ -914,6 +935,7 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p, double flops
                                                                                        p.triA, ea, Mp, Kp, As);
   oz_split_b_kernel<S><<<dim3(ceil_div_u(Np / 2, 32), ceil_div_u(Kp / 2, 32)), tb, 0, s>>>(p.k, p.n, p.B, p.ldb,
                                                                                            p.opB, p.triB, fb, Np, Kp, Bs);
+  prof_launch_end(s, "oz_split (exponents, slices)");
   bse_count_launch(4);
   BSE_LAUNCH_CHECK();
   OzArgs<cplx> z;
@@ -958,6 +980,7 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p, double f
   uint16_t* Bs = (uint16_t*)(base + (size_t)S * Mp * Kp * 2);
   int* ea = (int*)(base + (size_t)S * (Mp + Np) * Kp * 2);
   int* fb = ea + Mp;
+  prof_launch_begin(s);
   BSE_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (Mp + Np), s));
   dim3 tb(32, 8);
   oz_exp_d_kernel<<<dim3(ceil_div_u(p.k, 32), ceil_div_u(p.m, 32)), tb, 0, s>>>(p.m, p.k, p.A, p.lda, p.opA, p.triA, 1, ea);
@@ -966,6 +989,7 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p, double f
                                                                                     p.triA, 0, ea, Mp, Kp, As);
   oz_split_d_kernel<S><<<dim3(ceil_div_u(Kp, 32), ceil_div_u(Np, 32)), tb, 0, s>>>(p.k, p.n, p.B, p.ldb, p.opB,
                                                                                     p.triB, 1, fb, Np, Kp, Bs);
+  prof_launch_end(s, "oz_split (exponents, slices)");
   bse_count_launch(4);
   BSE_LAUNCH_CHECK();
   OzArgs<double> z;
