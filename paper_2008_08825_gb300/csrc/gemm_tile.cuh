@@ -195,7 +195,13 @@ __device__ __forceinline__ void gemm_tile(const GemmParams<T>& p, int64_t i0, in
 
 template <typename T, int BK>
 __global__ void __launch_bounds__(256, 2) gemm_kernel(const GemmParams<T> p) {
-  const int64_t i0 = (int64_t)blockIdx.y * GBM, j0 = (int64_t)blockIdx.x * GBN;
+  // longest tiles first: with a lower-triangular A a tile's k range grows with
+  // its row, with an upper-triangular B with its column, so those orders are
+  // reversed (CTAs start in increasing block order; the last wave is then
+  // made of the shortest tiles)
+  const int64_t by = p.triA == TRI_LO ? (int64_t)gridDim.y - 1 - blockIdx.y : (int64_t)blockIdx.y;
+  const int64_t bx = p.triB == TRI_UP ? (int64_t)gridDim.x - 1 - blockIdx.x : (int64_t)blockIdx.x;
+  const int64_t i0 = by * GBM, j0 = bx * GBN;
   if (i0 >= p.m || j0 >= p.n) return;
   if (p.lowerC && j0 > i0 + GBM - 1) return;
   if (p.status && *(volatile const int64_t*)p.status) return;
