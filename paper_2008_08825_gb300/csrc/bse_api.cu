@@ -158,7 +158,7 @@ static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k, int prec)
   b.lam = pl.take<double>(k);
   b.c1 = pl.take<double>(k);
   b.c2 = pl.take<double>(k);
-  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
+  b.tmp = pl.take<cplx>(backtransform_tmp_elems(k));
 }
 
 struct SvdBuffers {
@@ -202,7 +202,7 @@ static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k, int prec) {
   b.lam = pl.take<double>(k);
   b.c1 = pl.take<double>(k);
   b.c2 = pl.take<double>(k);
-  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
+  b.tmp = pl.take<cplx>(backtransform_tmp_elems(k));
 }
 
 // Alg. 1: M1 = A + B (full), A - B reduced in M, its eigenvectors Q, the square
@@ -245,7 +245,7 @@ static void carve_sqrt(Plan& pl, SqrtBuffers& b, int64_t n, int64_t k, int prec)
   b.lam = pl.take<double>(k);
   b.c1 = pl.take<double>(k);
   b.c2 = pl.take<double>(k);
-  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * n);
+  b.tmp = pl.take<cplx>(backtransform_tmp_elems(n));
 }
 
 // Tamm-Dancoff (B = 0): the Hermitian eigenproblem of A alone
@@ -274,7 +274,7 @@ static void carve_tda(Plan& pl, TdaBuffers& b, int64_t n, int64_t k) {
   b.lam = pl.take<double>(k);
   b.c1 = pl.take<double>(k);
   b.c2 = pl.take<double>(k);
-  b.tmp = pl.take<cplx>(2 * (size_t)backtransform_block() * backtransform_block() + 2 * (size_t)backtransform_block() * k);
+  b.tmp = pl.take<cplx>(backtransform_tmp_elems(k));
 }
 
 static size_t plan_bytes(int64_t n, int64_t k, int method, int prec) {

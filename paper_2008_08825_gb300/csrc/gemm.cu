@@ -68,10 +68,18 @@ static double useful_macs(const GemmParams<T>& p) {
   return (double)m * n * k;  // not used by the pipelines: dense count
 }
 
+static bool beta_nz(cplx b) { return b.x != 0.0 || b.y != 0.0; }
+static bool beta_nz(double b) { return b != 0.0; }
+static bool beta_nz(float b) { return b != 0.0f; }
+
 template <typename T, int BK>
 static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
   if (p.m <= 0 || p.n <= 0) return BSE_OK;
-  dim3 grid(ceil_div_u(p.n, GBN), ceil_div_u(p.m, GBM));
+  dim3 grid(ceil_div_u(p.n, GBN), ceil_div_u(p.m, GBM), p.kchunk > 0 ? ceil_div_u(p.k, p.kchunk) : 1);
+  if (p.kchunk > 0 && (p.kchunk % 64 != 0 || beta_nz(p.beta))) {
+    bse_internal_set_error("gemm: split-K needs kchunk % 64 == 0 and beta == 0");
+    return BSE_ERR_ARG;
+  }
   if (grid.y > 65535) {
     bse_internal_set_error("gemm: m too large for one launch");
     return BSE_ERR_ARG;
@@ -89,7 +97,7 @@ static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
 
 bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
   const OzWork oz = oz_current();
-  if (oz.ptr && p.opA != OPT && p.opB != OPT && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
+  if (oz.ptr && p.kchunk == 0 && p.opA != OPT && p.opB != OPT && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
     const bool prof = prof_current() != nullptr;
     if (prof) prof_gemm_begin(s);
     const double flops = useful_macs(p) * 8.0;
@@ -101,7 +109,7 @@ bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
 }
 bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) {
   const OzWork oz = oz_current();
-  if (oz.ptr && p.opA != OPC && p.opB != OPC && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
+  if (oz.ptr && p.kchunk == 0 && p.opA != OPC && p.opB != OPC && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
     const bool prof = prof_current() != nullptr;
     if (prof) prof_gemm_begin(s);
     const double flops = useful_macs(p) * 2.0;

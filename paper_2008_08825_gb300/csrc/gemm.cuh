@@ -38,6 +38,11 @@ struct GemmParams {
   const double* c2;
   T* Y;
   int64_t ldy;
+  // split-K (DFMA engine only): when kchunk > 0, grid layer z computes the k
+  // range [z kchunk, (z+1) kchunk) into C + z cstride (kchunk a multiple of
+  // 64, beta 0); the caller adds the layers
+  int64_t kchunk;
+  int64_t cstride;
 };
 
 template <typename T>
@@ -52,6 +57,7 @@ __host__ __device__ inline GemmParams<T> gemm_params(int64_t m, int64_t n, int64
   p.status = nullptr;
   p.epi = EPI_NONE;
   p.P = nullptr, p.ldp = 0, p.c1 = nullptr, p.c2 = nullptr, p.Y = nullptr, p.ldy = 0;
+  p.kchunk = 0, p.cstride = 0;
   return p;
 }
 

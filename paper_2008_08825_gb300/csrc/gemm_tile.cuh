@@ -44,7 +44,8 @@ constexpr int GBM = 64, GBN = 64;
 // products).  The caller guarantees i0 < m, j0 < n; on return the shared
 // staging buffers may be reused (the function ends with a barrier).
 template <typename T, int BK>
-__device__ __forceinline__ void gemm_tile(const GemmParams<T>& p, int64_t i0, int64_t j0) {
+__device__ __forceinline__ void gemm_tile(const GemmParams<T>& p, int64_t i0, int64_t j0, int64_t kz0 = 0,
+                                          int64_t kz1 = INT64_MAX, T* Cz = nullptr) {
   using N_ = Num<T>;
   constexpr int LA = GBM * BK / 256;
   constexpr int LB = GBN * BK / 256;
@@ -58,6 +59,8 @@ __device__ __forceinline__ void gemm_tile(const GemmParams<T>& p, int64_t i0, in
   if (p.triA == TRI_UP) kbeg = max(kbeg, i0);
   if (p.triB == TRI_LO) kbeg = max(kbeg, j0);
   if (p.triB == TRI_UP) kend = min(kend, j0 + GBN);
+  kbeg = max(kbeg, kz0);  // split-K layer (kz0, kz1 multiples of BK)
+  kend = min(kend, kz1);
   kbeg = (kbeg / BK) * BK;
   const int64_t nk = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
 
@@ -168,6 +171,7 @@ __device__ __forceinline__ void gemm_tile(const GemmParams<T>& p, int64_t i0, in
   }
 
   const bool use_beta = N_::nz(p.beta);
+  T* const Cout = Cz ? Cz : p.C;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int64_t j = j0 + ty + 16 * b;
@@ -185,8 +189,8 @@ __device__ __forceinline__ void gemm_tile(const GemmParams<T>& p, int64_t i0, in
         p.C[i + j * p.ldc] = N_::add(x1, x2);
         p.Y[i + j * p.ldy] = N_::add(x2, N_::rs(x1, -1.0));
       } else {
-        if (use_beta) v = N_::add(v, N_::mul(p.beta, p.C[i + j * p.ldc]));
-        p.C[i + j * p.ldc] = v;
+        if (use_beta) v = N_::add(v, N_::mul(p.beta, Cout[i + j * p.ldc]));
+        Cout[i + j * p.ldc] = v;
       }
     }
   }
@@ -205,7 +209,10 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(const GemmParams<T> p) {
   if (i0 >= p.m || j0 >= p.n) return;
   if (p.lowerC && j0 > i0 + GBM - 1) return;
   if (p.status && *(volatile const int64_t*)p.status) return;
-  gemm_tile<T, BK>(p, i0, j0);
+  const bool split = p.kchunk > 0;
+  const int64_t z = blockIdx.z;
+  gemm_tile<T, BK>(p, i0, j0, split ? z * p.kchunk : 0, split ? (z + 1) * p.kchunk : INT64_MAX,
+                   split ? p.C + z * p.cstride : p.C);
 }
 
 // All tiles of one product, computed by the calling CTA (batched solver).

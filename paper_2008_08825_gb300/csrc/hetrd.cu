@@ -23,9 +23,13 @@ constexpr int NBT = 32;    // panel width
 constexpr int RB = 64;     // rows per CTA (and threads) of the per-column row kernels
 constexpr int HCH = 512;   // column chunk of the Hermitian matvec
 constexpr int BTB = 128;   // reflectors per block in the back-transformation
+constexpr int GSPLIT = 64;  // split-K layers of the Gram product V^H V of a block
 
 int hetrd_panel() { return NBT; }
 int backtransform_block() { return BTB; }
+size_t backtransform_tmp_elems(int64_t k) {
+  return (size_t)(2 + GSPLIT) * BTB * BTB + 2 * (size_t)BTB * k;
+}
 static inline int64_t nchunks(int64_t m) { return (m + HCH - 1) / HCH; }
 size_t hetrd_part_elems(int64_t n) {
   const int64_t slots = (n + 63) / 64 > 2 * nchunks(n) ? (n + 63) / 64 : 2 * nchunks(n);
@@ -392,6 +396,15 @@ __global__ void larft_kernel(int bs, const cplx* __restrict__ G, int ldg, const 
   }
 }
 
+// out[e] = sum of the nl layers of `len` elements
+__global__ void sum_layers_kernel(int64_t len, int nl, const cplx* __restrict__ layers, cplx* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  cplx acc = layers[e];
+  for (int z = 1; z < nl; ++z) acc = cadd(acc, layers[e + z * len]);
+  out[e] = acc;
+}
+
 bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cplx* Vbuf, int64_t ldvb, int64_t c0,
                                  int64_t bs, int64_t r0, const cplx* tau, cplx* Vout, int64_t ldv, cplx* tmp,
                                  const int64_t* status) {
@@ -403,10 +416,22 @@ bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cpl
   cplx* T = G + bs * bs;         // bs x bs
   cplx* W1 = T + bs * bs;        // bs x k
   cplx* W2 = W1 + bs * k;        // bs x k
-  GemmParams<cplx> pg = gemm_params<cplx>(bs, bs, m, OPC, Vp, ldvb, OPN, Vp, ldvb, one, zero, G, bs);
+  cplx* Gl = W2 + bs * k;        // GSPLIT layers of bs x bs
+  // G = V^H V: a bs x bs output over the m rows of the block; as one GEMM it
+  // would run on (bs/64)^2 = 4 CTAs, so the k range is split into up to
+  // GSPLIT layers (DFMA engine, both precisions: it is ~0.1% of the flops)
+  // and the layers are added
+  const int64_t kc = ((m + GSPLIT - 1) / GSPLIT + 63) / 64 * 64;
+  const int nl = (int)((m + kc - 1) / kc);
+  GemmParams<cplx> pg = gemm_params<cplx>(bs, bs, m, OPC, Vp, ldvb, OPN, Vp, ldvb, one, zero, Gl, bs);
   pg.status = status;
+  pg.kchunk = kc;
+  pg.cstride = bs * bs;
   bse_status r = gemm_z(s, pg);
   if (r) return r;
+  sum_layers_kernel<<<ceil_div_u(bs * bs, 256), 256, 0, s>>>(bs * bs, nl, Gl, G);
+  bse_count_launch();
+  BSE_LAUNCH_CHECK();
   const int lt = (int)((bs + 31) / 32 * 32);
   larft_kernel<<<1, lt, 0, s>>>((int)bs, G, (int)bs, tau + c0, T, (int)bs, status);
   bse_count_launch();

@@ -57,6 +57,7 @@ struct HetrdWork {
 int hetrd_panel();
 // reflectors per block in the back-transformations (T factor of this width)
 int backtransform_block();
+size_t backtransform_tmp_elems(int64_t k);  // workspace of apply_block_reflector
 size_t hetrd_part_elems(int64_t n);
 bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const HetrdWork& w,
                        const int64_t* status);
