@@ -16,6 +16,8 @@
 // HBM (n'^2 complex MACs over n'^2 * 16 bytes needs 3.4 TFLOP/s to saturate
 // 6.8 TB/s; the part delivers 1.2), so the one-stage reduction does the same
 // FP64 work as a band reduction and saves its second back-transformation.
+#include <cmath>
+
 #include "kernels.cuh"
 #include "prof.cuh"
 
@@ -24,11 +26,35 @@ constexpr int RB = 64;     // rows per CTA (and threads) of the per-column row k
 constexpr int HCH = 512;   // column chunk of the Hermitian matvec
 constexpr int BTB = 128;   // reflectors per block in the back-transformation
 constexpr int GSPLIT = 64;  // split-K layers of the Gram product V^H V of a block
+constexpr int WSPLIT = 8;   // at most this many split-K layers of W1 = V^H Z
 
 int hetrd_panel() { return NBT; }
 int backtransform_block() { return BTB; }
 size_t backtransform_tmp_elems(int64_t k) {
-  return (size_t)(2 + GSPLIT) * BTB * BTB + 2 * (size_t)BTB * k;
+  return (size_t)(2 + GSPLIT) * BTB * BTB + (2 + WSPLIT) * (size_t)BTB * k;
+}
+
+// Split-K layers for a product whose tiles do not fill the GPU: the count
+// s <= WSPLIT that brings tiles * s closest to whole waves of 2 CTAs per SM.
+static int split_layers(int64_t tiles) {
+  static int slots = 0;
+  if (!slots) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 148;
+    }
+    slots = 2 * sms;
+  }
+  if (tiles >= 4 * slots) return 1;
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= WSPLIT; ++s) {
+    const double work = (double)tiles * s;
+    const double eff = work / (slots * std::ceil(work / slots));
+    if (eff > best_eff + 0.02) best = s, best_eff = eff;
+  }
+  return best;
 }
 static inline int64_t nchunks(int64_t m) { return (m + HCH - 1) / HCH; }
 size_t hetrd_part_elems(int64_t n) {
@@ -438,7 +464,24 @@ bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cpl
   BSE_LAUNCH_CHECK();
   GemmParams<cplx> p1 = gemm_params<cplx>(bs, k, m, OPC, Vp, ldvb, OPN, Vout + r0, ldv, one, zero, W1, bs);
   p1.status = status;
-  if ((r = gemm_z(s, p1))) return r;
+  // W1 = V^H Z has (bs/64) x (k/64) tiles of depth m; on the DFMA engine
+  // (the tensor-core engine keeps its own tiling) split k for whole waves
+  const OzWork oz = oz_current();
+  const bool on_tc = oz.ptr && (double)bs * k * m >= (double)oz.min_mnk;
+  const int ws = on_tc ? 1 : split_layers(((bs + 63) / 64) * ((k + 63) / 64));
+  if (ws > 1 && m >= 64 * ws) {
+    cplx* Wl = Gl + (size_t)GSPLIT * bs * bs;  // ws layers of bs x k
+    p1.C = Wl;
+    p1.kchunk = ((m + ws - 1) / ws + 63) / 64 * 64;
+    p1.cstride = bs * k;
+    if ((r = gemm_z(s, p1))) return r;
+    const int nl = (int)((m + p1.kchunk - 1) / p1.kchunk);
+    sum_layers_kernel<<<ceil_div_u(bs * k, 256), 256, 0, s>>>(bs * k, nl, Wl, W1);
+    bse_count_launch();
+    BSE_LAUNCH_CHECK();
+  } else if ((r = gemm_z(s, p1))) {
+    return r;
+  }
   GemmParams<cplx> p2 = gemm_params<cplx>(bs, k, bs, OPN, T, bs, OPN, W1, bs, one, zero, W2, bs);
   p2.triA = TRI_UP;
   p2.status = status;
