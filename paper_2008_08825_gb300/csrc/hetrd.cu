@@ -9,7 +9,7 @@
 //   2. gets the reflector H_j = I - tau v v^H with H_j^H x = beta e_1,
 //      beta real (tr_house), so T is real,
 //   3. w = tau (A22 v - V (W^H v) - W (V^H v)) with A22 v from the lower
-//      triangle, 64 x 64 tiles, each tile read once (tr_hemv_tiled),
+//      triangle, 64 x 64 tiles, each tile read once (tr_hemv_strip),
 //   4. w += -tau/2 (w^H v) v  -- so that H_j^H A H_j = A - v w^H - w v^H.
 // After the panel, the trailing lower triangle takes the rank-2*NBT update
 // through the GEMM engine.  On GB300 step 3 is bound by the FP64 pipe, not by
@@ -23,7 +23,6 @@
 
 constexpr int NBT = 32;    // panel width
 constexpr int RB = 64;     // rows per CTA (and threads) of the per-column row kernels
-constexpr int HCH = 512;   // column chunk of the Hermitian matvec
 constexpr int BTB = 128;   // reflectors per block in the back-transformation
 constexpr int GSPLIT = 64;  // split-K layers of the Gram product V^H V of a block
 constexpr int WSPLIT = 8;   // at most this many split-K layers of W1 = V^H Z
@@ -56,10 +55,15 @@ static int split_layers(int64_t tiles) {
   }
   return best;
 }
-static inline int64_t nchunks(int64_t m) { return (m + HCH - 1) / HCH; }
+constexpr int HR = 8;      // row tiles per CTA of the strip matvec
+// partial-sum slots of the matvec: one per 64-wide column strip (row
+// products) plus one per chunk of HR row tiles (column products)
+static inline int64_t hemv_slots(int64_t n) {
+  const int64_t nt = (n + 63) / 64;
+  return nt + (nt + HR - 1) / HR;
+}
 size_t hetrd_part_elems(int64_t n) {
-  const int64_t slots = (n + 63) / 64 > 2 * nchunks(n) ? (n + 63) / 64 : 2 * nchunks(n);
-  return (size_t)(slots + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64;
+  return (size_t)(hemv_slots(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -159,85 +163,85 @@ __global__ void __launch_bounds__(RB) tr_house(int64_t n, int64_t j, const cplx*
   if (r < n) V[IDX2(r, j, ldv)] = (r == j + 1) ? mkc(1.0, 0.0) : cmul(A[IDX2(r, j, lda)], hs.scal);
 }
 
-// 3. y = A22 v from the lower triangle in 64 x 64 tiles, one CTA per tile of
-// the lower triangle: each tile is read once and gives both its row sums
-// (A v) and, off the diagonal, its column sums (A^H v).  Slot s of the
-// partial buffer for an index i in block b is written by exactly one tile:
-// (b, s) for s < b (row sums), (b, b) (row sums + strict-lower column
-// sums), (s, b) for s > b (column sums); the assembly adds the slots.
+// 3. y = A22 v from the lower triangle in 64 x 64 tiles: each tile is read
+// once and gives both its row sums (A v) and, off the diagonal, its column
+// sums (A^H v).
 constexpr int HT = 64;
 constexpr int HEMV_SMEM = (int)sizeof(cplx) * HT * (HT + 1);  // 66,560 bytes of dynamic shared memory
 
-__device__ __forceinline__ void tile_of(int64_t L, int64_t* bi, int64_t* bj) {
-  int64_t b = (int64_t)((sqrt(8.0 * (double)L + 1.0) - 1.0) * 0.5);
-  while ((b + 1) * (b + 2) / 2 <= L) ++b;
-  while (b * (b + 1) / 2 > L) --b;
-  *bi = b;
-  *bj = L - b * (b + 1) / 2;
-}
-
-__global__ void __launch_bounds__(256) tr_hemv_tiled(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
+// Column strips: CTA (ch, bj) takes the row tiles
+// bi in [bj + ch HR, min(nt, bj + (ch+1) HR)) of the 64-wide column strip bj.
+// Thread (row r, column eighth q) reads 8 entries of its row per tile; the
+// row products of a tile go to slot bj (one writer per row), the column
+// products accumulate in registers over the CTA's tiles and, after one
+// shared-memory reduction, go to slot nt + ch.  Per entry: two complex
+// multiply-adds and no shared-memory staging (a tile-per-CTA form that
+// staged every column product ran at 64% of the DFMA rate).
+__global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
                                                      const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
                                                      int64_t ldpart, const int64_t* status) {
   extern __shared__ cplx T[];  // column partials, T[c * (HT + 1) + r]
-  __shared__ cplx vr[HT], vc[HT];
-  __shared__ cplx rs[4][HT];
-  __shared__ cplx cs[4][HT];
+  __shared__ cplx vc[HT];
+  __shared__ cplx rs[8][HT];
   if (*(volatile const int64_t*)status) return;
   const int64_t base = j + 1, m = n - base;
-  int64_t bi, bj;
-  tile_of(blockIdx.x, &bi, &bj);
-  const int64_t r0 = bi * HT, c0 = bj * HT;
-  const int tid = threadIdx.x;
-  if (tid < HT) {
-    vr[tid] = (r0 + tid < m) ? V[IDX2(base + r0 + tid, j, ldv)] : mkc(0.0, 0.0);
-    vc[tid] = (c0 + tid < m) ? V[IDX2(base + c0 + tid, j, ldv)] : mkc(0.0, 0.0);
-  }
+  const int64_t nt = (m + HT - 1) / HT;
+  const int64_t bj = blockIdx.y, bi0 = bj + (int64_t)blockIdx.x * HR;
+  if (bj >= nt || bi0 >= nt) return;
+  const int64_t bi1 = bi0 + HR < nt ? bi0 + HR : nt;
+  const int64_t c0 = bj * HT;
+  const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;  // row, column eighth
+  if (tid < HT) vc[tid] = (c0 + tid < m) ? V[IDX2(base + c0 + tid, j, ldv)] : mkc(0.0, 0.0);
   __syncthreads();
-  // load: thread (row r, column quarter q), coalesced along rows
-  const int r = tid & 63, q = tid >> 6;
-  const int64_t gr = r0 + r;
-  const bool diag = bi == bj;
-  const cplx* Ar = A + IDX2(base + gr, base + c0, lda);
-  cplx av[16];
+  cplx colacc[8];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int c = q * 16 + u;
-    const bool in = gr < m && c0 + c < m && (!diag || r >= c);
-    av[u] = in ? __ldg(Ar + (int64_t)c * lda) : mkc(0.0, 0.0);
-  }
-  const cplx vrr = vr[r];
-  cplx rowacc = mkc(0.0, 0.0);
+  for (int u = 0; u < 8; ++u) colacc[u] = mkc(0.0, 0.0);
+  for (int64_t bi = bi0; bi < bi1; ++bi) {
+    const int64_t r0 = bi * HT, gr = r0 + r;
+    const bool diag = bi == bj;
+    const cplx vrr = gr < m ? V[IDX2(base + gr, j, ldv)] : mkc(0.0, 0.0);
+    const cplx* Ar = A + IDX2(base + gr, base + c0, lda);
+    cplx av[8];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int c = q * 16 + u;
-    cfma(rowacc, av[u], vc[c]);
-    cplx t = mkc(0.0, 0.0);
-    if (!diag || r > c) cfma_cj(t, av[u], vrr);
-    T[c * (HT + 1) + r] = t;
+    for (int u = 0; u < 8; ++u) {
+      const int c = q * 8 + u;
+      const bool in = gr < m && c0 + c < m && (!diag || r >= c);
+      av[u] = in ? __ldg(Ar + (int64_t)c * lda) : mkc(0.0, 0.0);
+    }
+    cplx rowacc = mkc(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = q * 8 + u;
+      cfma(rowacc, av[u], vc[c]);
+      if (!diag || r > c) cfma_cj(colacc[u], av[u], vrr);
+    }
+    rs[q][r] = rowacc;
+    __syncthreads();
+    if (tid < HT && r0 + tid < m) {
+      cplx y = rs[0][tid];
+#pragma unroll
+      for (int e = 1; e < 8; ++e) y = cadd(y, rs[e][tid]);
+      part[r0 + tid + bj * ldpart] = y;
+    }
+    __syncthreads();
   }
-  rs[q][r] = rowacc;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) T[(q * 8 + u) * (HT + 1) + r] = colacc[u];
   __syncthreads();
-  // column sums: thread (column c, row quarter q) adds 16 staged partials
   {
+    // column c: thread (c, eighth q) adds rows q*8 .. q*8+7, then the 8 eighths
     const int c = tid & 63;
     cplx acc = mkc(0.0, 0.0);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc = cadd(acc, T[c * (HT + 1) + q * 16 + u]);
-    cs[q][c] = acc;
+    for (int u = 0; u < 8; ++u) acc = cadd(acc, T[c * (HT + 1) + q * 8 + u]);
+    rs[q][c] = acc;
   }
   __syncthreads();
-  if (tid < HT) {
-    const int64_t i = r0 + tid;
-    if (i < m) {
-      cplx y = cadd(cadd(rs[0][tid], rs[1][tid]), cadd(rs[2][tid], rs[3][tid]));
-      if (diag) y = cadd(y, cadd(cadd(cs[0][tid], cs[1][tid]), cadd(cs[2][tid], cs[3][tid])));
-      part[i + bj * ldpart] = y;
-    }
-  } else if (tid < 2 * HT && !diag) {
-    const int c = tid - HT;
-    const int64_t i = c0 + c;
-    if (i < m) part[i + bi * ldpart] = cadd(cadd(cs[0][c], cs[1][c]), cadd(cs[2][c], cs[3][c]));
+  if (tid < HT && c0 + tid < m) {
+    cplx y = rs[0][tid];
+#pragma unroll
+    for (int e = 1; e < 8; ++e) y = cadd(y, rs[e][tid]);
+    part[c0 + tid + (nt + blockIdx.x) * ldpart] = y;
   }
 }
 
@@ -280,7 +284,11 @@ __global__ void __launch_bounds__(256) tr_w_assemble(int64_t n, int64_t p, int64
   const int64_t r = (int64_t)blockIdx.x * AR + rl;
   cplx y = mkc(0.0, 0.0);
   if (r < m) {
-    for (int c = qq; c < nch; c += 4) y = cadd(y, part[r + c * ldpart]);
+    // row products of strips 0..b, column products of the chunks of strip b
+    const int b = (int)(r / HT);
+    const int nchk = (nch - b + HR - 1) / HR;
+    for (int c = qq; c <= b; c += 4) y = cadd(y, part[r + c * ldpart]);
+    for (int c = qq; c < nchk; c += 4) y = cadd(y, part[r + (nch + c) * ldpart]);
     const int64_t gr = base + r;
     for (int q = qq; q < jj; q += 4) {
       y = csub(y, cmul(V[IDX2(gr, p + q, ldv)], s1[q]));
@@ -341,14 +349,14 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
   if (n <= 0) return BSE_OK;
   static bool attr = false;
   if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(tr_hemv_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, HEMV_SMEM));
+    BSE_CUDA(cudaFuncSetAttribute(tr_hemv_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, HEMV_SMEM));
     attr = true;
   }
   const int64_t ldv = n, ldw = n;
   BSE_CUDA(cudaMemsetAsync(w.V, 0, sizeof(cplx) * n * n, s));
   const int64_t ldpart = n + 1;
-  cplx* part = w.part;                                     // 2 * nchunks columns of length ldpart
-  const int64_t slots = (n + 63) / 64 > 2 * nchunks(n) ? (n + 63) / 64 : 2 * nchunks(n);
+  cplx* part = w.part;  // hemv_slots(n) columns of length ldpart
+  const int64_t slots = hemv_slots(n);
   double* npart = (double*)(w.part + slots * ldpart);
   double* dpart = npart + (n / RB + 2);
   cplx* s12 = w.small;
@@ -364,9 +372,9 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       const int64_t nt = (m + HT - 1) / HT;  // tile rows; partial slots
       {
         prof_launch_begin(s);
-        tr_hemv_tiled<<<(unsigned)(nt * (nt + 1) / 2), 256, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart,
-                                                                            status);
-        prof_launch_end(s, "tr_hemv_tiled");
+        const dim3 hg((unsigned)((nt + HR - 1) / HR), (unsigned)nt);
+        tr_hemv_strip<<<hg, 512, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, status);
+        prof_launch_end(s, "tr_hemv_strip");
         bse_count_launch();
         BSE_LAUNCH_CHECK();
       }
