@@ -448,8 +448,13 @@ __global__ void __launch_bounds__(256, 1) oz_mma_kernel(const OzArgs<T> z) {
 // tmem_empty per fold.  Every wait is bounded: on timeout the CTA records
 // BSE_ERR_TIMEOUT in the status word (when given), stops issuing, drains what
 // it started and frees its TMEM.
+// Stage shape: two stages of 32 k' (rows of 64 bytes, 64-byte swizzle).  Four
+// stages of 16 k' (32-byte rows and swizzle; UM_BK = 16, UM_STAGES = 4) measured
+// the same speed on this part, so the refill latency is not what bounds it.
 constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 32, UM_STAGES = 2;
 constexpr int UM_SLICE_A = UM_BM * UM_BK * 2, UM_SLICE_B = UM_BN * UM_BK * 2;  // 8 KB, 4 KB
+constexpr int UM_FOLD = 512 / UM_BK;  // k-tiles per fold (512 k', the exactness bound)
+constexpr int UM_ROWB = UM_BK * 2;    // bytes per k-major tile row
 constexpr long long UM_WAIT_CYCLES = 2000000000LL;                               // about 1 s
 
 template <int S>
@@ -482,12 +487,13 @@ __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity, volatile 
   }
 }
 
-// K-major operand tile in shared memory, 64-byte swizzle: rows of 64 bytes,
-// 8-row groups 512 bytes apart (stride byte offset); the leading byte offset
-// is unused for swizzled K-major tiles; descriptor version 1; layout 4 = 64B.
+// K-major operand tile in shared memory, swizzled rows of UM_ROWB bytes (32:
+// layout 6, 64: layout 4), 8-row groups 8 UM_ROWB bytes apart (stride byte
+// offset); the leading byte offset is unused for swizzled K-major tiles;
+// descriptor version 1.
 __device__ __forceinline__ uint64_t um_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * UM_ROWB) >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)(UM_ROWB == 64 ? 4 : 6) << 61);
 }
 
 // instruction descriptors: FP32 accumulate, BF16 A and B, both K-major, N, M
@@ -522,15 +528,16 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
   if (p.triB == TRI_UP) ke = min(ke, jc0 + UM_BN / XF);
   const int64_t kb2 = (XF * kb / UM_BK) * UM_BK, ke2 = XF * ke;
   const int ntile = ke2 > kb2 ? (int)((ke2 - kb2 + UM_BK - 1) / UM_BK) : 0;
-  const int nfold = (ntile + OZ_FOLD - 1) / OZ_FOLD;
+  const int nfold = (ntile + UM_FOLD - 1) / UM_FOLD;
 
   unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(base + UM_STAGES * L::STAGE);  // full[2] empty[2] tfull tempty drain
-  uint32_t* tslot = (uint32_t*)(bars + 8);
+  uint64_t* bars = (uint64_t*)(base + UM_STAGES * L::STAGE);  // full[S] empty[S] tfull tempty drain
+  uint32_t* tslot = (uint32_t*)(bars + 2 * UM_STAGES + 4);
   int* abort_flag = (int*)(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
-  const uint32_t tfull = smem_u32(bars + 4), tempty = smem_u32(bars + 5), drain = smem_u32(bars + 6);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + UM_STAGES);
+  const uint32_t tfull = smem_u32(bars + 2 * UM_STAGES), tempty = smem_u32(bars + 2 * UM_STAGES + 1);
+  const uint32_t drain = smem_u32(bars + 2 * UM_STAGES + 2);
   if (threadIdx.x == 0) {
     for (int q = 0; q < UM_STAGES; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * q));
@@ -588,8 +595,8 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     bool ok = true;
     for (int kt = 0; kt < ntile && ok; ++kt) {
       const int st = kt % UM_STAGES;
-      if (kt % OZ_FOLD == 0) {  // the sets are zero (initially, or read and cleared by the last fold)
-        ok = um_wait(tempty, (kt / OZ_FOLD) & 1, ab, ab);
+      if (kt % UM_FOLD == 0) {  // the sets are zero (initially, or read and cleared by the last fold)
+        ok = um_wait(tempty, (kt / UM_FOLD) & 1, ab, ab);
         if (!ok) break;
       }
       ok = um_wait(full0 + 8 * st, (kt / UM_STAGES) & 1, ab, ab);
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
       if (!ok) break;
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty0 + 8 * st)
                    : "memory");
-      if ((kt + 1) % OZ_FOLD == 0 || kt + 1 == ntile)
+      if ((kt + 1) % UM_FOLD == 0 || kt + 1 == ntile)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(tfull)
                      : "memory");
     }
@@ -874,7 +881,8 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// slices [S][rows][Kp] bf16 as a 3-D tensor (k', row, slice); box (32, box_rows, S), 64-byte swizzle
+// slices [S][rows][Kp] bf16 as a 3-D tensor (k', row, slice); box (UM_BK, box_rows, S), swizzled as
+// the descriptors expect
 static bool slice_map(CUtensorMap* m, const void* base, int S, int64_t rows, int64_t Kp, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
@@ -883,7 +891,8 @@ static bool slice_map(CUtensorMap* m, const void* base, int S, int64_t rows, int
   const cuuint32_t box[3] = {(cuuint32_t)UM_BK, (cuuint32_t)box_rows, (cuuint32_t)S};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, UM_ROWB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
