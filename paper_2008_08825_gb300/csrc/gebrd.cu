@@ -129,11 +129,37 @@ __global__ void __launch_bounds__(BRB) bd_house_left(BdArgs a, int nparts) {
 // slot = row block.  Thread (row r, column quarter q) holds 16 entries.
 constexpr int BT64 = 64;
 
-__global__ void __launch_bounds__(BRB) bd_gemv_c(BdArgs a) {
+// the small panel dots out[q] = sum_{r in [r0, n)} conj(colA_q(r)) vec(r) (q < nA)
+// and out[NBB + q] likewise over colB, done by the extra row of CTAs of a
+// matrix-vector launch (outputs first, first + stride, ...): they run beside
+// the matvec instead of as a launch of their own
+__device__ void bd_dots_role(int64_t n, int64_t r0, int nA, const cplx* colA, int64_t offA, int nB,
+                             const cplx* colB, int64_t offB, const cplx* vec, cplx* out, int first, int stride,
+                             double* red) {
+  for (int d = first; d < nA + nB; d += stride) {
+    const int which = d < nA ? 0 : 1;
+    const int q = which == 0 ? d : d - nA;
+    const cplx* col = which == 0 ? colA + (offA + q) * n : colB + (offB + q) * n;
+    cplx acc = mkc(0.0, 0.0);
+    for (int64_t r = r0 + threadIdx.x; r < n; r += blockDim.x) cfma_cj(acc, col[r], vec[r]);
+    const double sx = bsum(acc.x, red);
+    const double sy = bsum(acc.y, red);
+    if (threadIdx.x == 0) out[which * NBB + q] = mkc(sx, sy);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(BRB) bd_gemv_c(BdArgs a, int dots) {
   __shared__ cplx us[BT64];
   __shared__ cplx cs[4][BT64];
+  __shared__ double red[32];
   BD_GUARD();
   const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
+  if (dots && blockIdx.y == gridDim.y - 1) {  // U^H u and X^H u of the panel so far
+    const int ii = (int)(i - a.p);
+    bd_dots_role(n, i, ii, a.U, a.p, ii, a.X, 0, a.U + i * ld, a.s, blockIdx.x, gridDim.x, red);
+    return;
+  }
   const int64_t r0 = i + (int64_t)blockIdx.y * BT64, c0 = i + 1 + (int64_t)blockIdx.x * BT64;
   const int tid = threadIdx.x;
   if (tid < BT64) us[tid] = (r0 + tid < n) ? a.U[IDX2(r0 + tid, i, ld)] : mkc(0.0, 0.0);
@@ -157,22 +183,6 @@ __global__ void __launch_bounds__(BRB) bd_gemv_c(BdArgs a) {
   }
 }
 
-// generic small dot: out = sum_{r in [r0, n)} conj(col(r)) vec(r); one CTA per output
-__global__ void __launch_bounds__(BRB) bd_dots(BdArgs a, int64_t r0, int nA, const cplx* colA, int64_t offA,
-                                               int nB, const cplx* colB, int64_t offB, const cplx* vec, cplx* out) {
-  __shared__ double red[32];
-  BD_GUARD();
-  const int64_t n = a.n, ld = n;
-  const int which = blockIdx.x < nA ? 0 : 1;
-  const int q = which == 0 ? blockIdx.x : blockIdx.x - nA;
-  const cplx* col = which == 0 ? colA + (offA + q) * ld : colB + (offB + q) * ld;
-  cplx acc = mkc(0.0, 0.0);
-  for (int64_t r = r0 + threadIdx.x; r < n; r += BRB) cfma_cj(acc, col[r], vec[r]);
-  const double sx = bsum(acc.x, red);
-  const double sy = bsum(acc.y, red);
-  if (threadIdx.x == 0) out[which * NBB + q] = mkc(sx, sy);
-  (void)nB;
-}
 
 // 1d. y(c) = tauq (sum parts - Y s_U - V s_X), c > i -> Y(c, ii); 64 entries
 // per CTA, 4 threads per entry
@@ -248,11 +258,17 @@ __global__ void __launch_bounds__(BRB) bd_house_right(BdArgs a, int nparts) {
 
 // 2c. row partials of A v over rows > i, columns > i: 64 x 64 tiles, slot =
 // column block.
-__global__ void __launch_bounds__(BRB) bd_gemv_n(BdArgs a) {
+__global__ void __launch_bounds__(BRB) bd_gemv_n(BdArgs a, int dots) {
   __shared__ cplx vs[BT64];
   __shared__ cplx rs[4][BT64];
+  __shared__ double red[32];
   BD_GUARD();
   const int64_t n = a.n, i = a.i, ld = n, ldp = n + 1;
+  if (dots && blockIdx.y == gridDim.y - 1) {  // Y^H v and V^H v of the panel so far
+    const int ii = (int)(i - a.p);
+    bd_dots_role(n, i + 1, ii + 1, a.Y, 0, ii, a.Vr, a.p, a.Vr + i * ld, a.s, blockIdx.x, gridDim.x, red);
+    return;
+  }
   const int64_t r0 = i + 1 + (int64_t)blockIdx.y * BT64, c0 = i + 1 + (int64_t)blockIdx.x * BT64;
   const int tid = threadIdx.x;
   if (tid < BT64) vs[tid] = (c0 + tid < n) ? a.Vr[IDX2(c0 + tid, i, ld)] : mkc(0.0, 0.0);
@@ -339,18 +355,16 @@ bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const Ge
       if (i == n - 1) break;
       const int64_t m = n - i - 1;  // trailing columns / rows
       // y = tauq (A^H u - Y (U^H u) - V (X^H u))
-      dim3 gc(ceil_div_u(m, BT64), ceil_div_u(n - i, BT64));
-      BLAUNCH(bd_gemv_c, gc, a);
-      if (ii > 0) BLAUNCH(bd_dots, 2 * ii, a, i, ii, w.U, p, ii, w.X, (int64_t)0, w.U + i * ld, w.small);
+      dim3 gc(ceil_div_u(m, BT64), ceil_div_u(n - i, BT64) + (ii > 0 ? 1 : 0));
+      BLAUNCH(bd_gemv_c, gc, a, ii > 0 ? 1 : 0);
       BLAUNCH(bd_y_assemble, ceil_div_u(m, AR), a, (int)ceil_div_u(n - i, BT64));
       // row update and right reflector
       const unsigned gm = ceil_div_u(m, BRB);
       BLAUNCH(bd_row_update, gm, a);
       BLAUNCH(bd_house_right, gm, a, (int)gm);
       // x = taup (A v - U (Y^H v) - X (V^H v))
-      dim3 gn(ceil_div_u(m, BT64), ceil_div_u(m, BT64));
-      BLAUNCH(bd_gemv_n, gn, a);
-      BLAUNCH(bd_dots, 2 * ii + 1, a, i + 1, ii + 1, w.Y, (int64_t)0, ii, w.Vr, p, w.Vr + i * ld, w.small);
+      dim3 gn(ceil_div_u(m, BT64), ceil_div_u(m, BT64) + 1);
+      BLAUNCH(bd_gemv_n, gn, a, 1);
       BLAUNCH(bd_x_assemble, ceil_div_u(m, AR), a, (int)ceil_div_u(m, BT64));
     }
     const int64_t t0 = p + bs, mt = n - t0;

@@ -177,15 +177,31 @@ constexpr int HEMV_SMEM = (int)sizeof(cplx) * HT * (HT + 1);  // 66,560 bytes of
 // shared-memory reduction, go to slot nt + ch.  Per entry: two complex
 // multiply-adds and no shared-memory staging (a tile-per-CTA form that
 // staged every column product ran at 64% of the DFMA rate).
+// With jj > 0 an extra row of CTAs (blockIdx.y == nt) computes the panel dots
+// s1 = W^H v and s2 = V_panel^H v (over rows >= j+1) beside the matvec.
 __global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
                                                      const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
-                                                     int64_t ldpart, const int64_t* status) {
+                                                     int64_t ldpart, int64_t p, int jj, const cplx* __restrict__ W,
+                                                     int64_t ldw, cplx* __restrict__ s12, const int64_t* status) {
   extern __shared__ cplx T[];  // column partials, T[c * (HT + 1) + r]
   __shared__ cplx vc[HT];
   __shared__ cplx rs[8][HT];
+  __shared__ double red[32];
   if (*(volatile const int64_t*)status) return;
   const int64_t base = j + 1, m = n - base;
   const int64_t nt = (m + HT - 1) / HT;
+  if (jj > 0 && (int64_t)blockIdx.y == nt) {
+    for (int d = blockIdx.x; d < 2 * jj; d += gridDim.x) {
+      const int q = d % jj, which = d / jj;  // which 0: W, 1: V
+      const cplx* col = which == 0 ? W + IDX2(0, q, ldw) : V + IDX2(0, p + q, ldv);
+      cplx acc = mkc(0.0, 0.0);
+      for (int64_t r = j + 1 + threadIdx.x; r < n; r += blockDim.x) cfma_cj(acc, col[r], V[IDX2(r, j, ldv)]);
+      const cplx sv = block_sum_c(acc, red);
+      if (threadIdx.x == 0) s12[which * NBT + q] = sv;
+      __syncthreads();
+    }
+    return;
+  }
   const int64_t bj = blockIdx.y, bi0 = bj + (int64_t)blockIdx.x * HR;
   if (bj >= nt || bi0 >= nt) return;
   const int64_t bi1 = bi0 + HR < nt ? bi0 + HR : nt;
@@ -243,21 +259,6 @@ __global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const
     for (int e = 1; e < 8; ++e) y = cadd(y, rs[e][tid]);
     part[c0 + tid + (nt + blockIdx.x) * ldpart] = y;
   }
-}
-
-// 3c. s1 = W^H v, s2 = V_panel^H v over rows >= j+1 (one CTA per output)
-__global__ void __launch_bounds__(256) tr_panel_dots(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
-                                                    int64_t ldv, const cplx* __restrict__ W, int64_t ldw,
-                                                    cplx* __restrict__ s12, const int64_t* status) {
-  __shared__ double red[32];
-  if (*(volatile const int64_t*)status) return;
-  const int jj = (int)(j - p);
-  const int q = blockIdx.x % jj, which = blockIdx.x / jj;  // which 0: W, 1: V
-  const cplx* col = which == 0 ? W + IDX2(0, q, ldw) : V + IDX2(0, p + q, ldv);
-  cplx acc = mkc(0.0, 0.0);
-  for (int64_t r = j + 1 + threadIdx.x; r < n; r += blockDim.x) cfma_cj(acc, col[r], V[IDX2(r, j, ldv)]);
-  const cplx s = block_sum_c(acc, red);
-  if (threadIdx.x == 0) s12[which * NBT + q] = s;
 }
 
 // 3d. w = tau (y - V s1 - W s2), stored in W(:, jj); partial sums of w^H v.
@@ -372,15 +373,14 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       const int64_t nt = (m + HT - 1) / HT;  // tile rows; partial slots
       {
         prof_launch_begin(s);
-        const dim3 hg((unsigned)((nt + HR - 1) / HR), (unsigned)nt);
-        tr_hemv_strip<<<hg, 512, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, status);
+        const int jj = (int)(j - p);
+        const dim3 hg((unsigned)((nt + HR - 1) / HR), (unsigned)(nt + (jj > 0 ? 1 : 0)));
+        tr_hemv_strip<<<hg, 512, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, p, jj, w.W, ldw, s12, status);
         prof_launch_end(s, "tr_hemv_strip");
         bse_count_launch();
         BSE_LAUNCH_CHECK();
       }
       const int64_t nch = nt;
-      const int jj = (int)(j - p);
-      if (jj > 0) LAUNCH(tr_panel_dots, 2 * jj, 256, n, p, j, w.V, ldv, w.W, ldw, s12, status);
       const unsigned ga = ceil_div_u(m, AR);
       LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, s12, w.tau, dpart,
              status);
