@@ -42,3 +42,34 @@ def test_null_handle_is_an_argument_error(lib):
     assert lib.bse_solve_chol(None, 4, None, 4, None, 4, 1, 4, 0, None, None, 4, None, 4, None, None) == 1
     assert lib.bse_grad(None, 4, 1, None, 4, None, 4, None, None, 4, None, 4, None) == 1
     assert b"handle" in lib.bse_last_error()
+
+
+def test_workspace_sizes_per_method(lib):
+    """TDA needs least, CHOL less than SVD and SQRT (eight n x n complex
+    buffers plus the full tridiagonal work); sizes grow with n; the mixed form
+    adds the slice workspace of the tensor-core products."""
+    def ws(n, method, prec=0):
+        b = ctypes.c_size_t(0)
+        assert lib.bse_workspace_size(n, method, prec, ctypes.byref(b)) == 0
+        return b.value
+
+    n = 1024
+    chol, svd, sqrt, tda = ws(n, 0), ws(n, 1), ws(n, 2), ws(n, 3)
+    assert tda < chol < min(svd, sqrt)
+    assert sqrt >= 8 * n * n * 16
+    for m in range(4):
+        assert ws(n, m) <= ws(2 * n, m)
+    assert ws(n, 0, 1) > chol + 8 * 2 * (2 * n) * (n + 2 * n)  # 8 BF16 slices of both operands
+
+
+def test_noalloc_host_checks_need_no_gpu(lib):
+    """Argument checks of the allocation-free entry point run before any CUDA
+    call: n above the limit gives BSE_ERR_TOO_LARGE, bad k an argument error,
+    n = 0 success; none of them touches a device."""
+    lib.bse_solve_chol_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 7
+    lib.bse_solve_chol_noalloc.restype = ctypes.c_int
+    assert lib.bse_solve_chol_noalloc(bse.NOALLOC_MAX_N + 1, 1, None, None, None, None, None, None, None) == 10
+    assert lib.bse_solve_chol_noalloc(8, 9, None, None, None, None, None, None, None) == 1
+    assert lib.bse_solve_chol_noalloc(8, -1, None, None, None, None, None, None, None) == 1
+    assert lib.bse_solve_chol_noalloc(0, 0, None, None, None, None, None, None, None) == 0
+    assert lib.bse_solve_chol_noalloc(8, 2, None, None, None, None, None, None, None) == 1  # NULL pointers
