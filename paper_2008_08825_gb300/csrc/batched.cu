@@ -813,13 +813,10 @@ __global__ void __launch_bounds__(BT, 1) batched_chol_kernel(const BatchDesc* __
 size_t batched_smem_bytes() { return sizeof(cplx) * (2048 + 2 * CNB * CLD); }
 
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid, int method) {
-  static bool attr = false;
   const size_t smem = batched_smem_bytes();
-  if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(batched_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BSE_CUDA(cudaFuncSetAttribute(batched_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  bse_status r = set_smem_attr((const void*)batched_chol_kernel, (int)smem);
+  if (!r) r = set_smem_attr((const void*)batched_svd_kernel, (int)smem);
+  if (r) return r;
   BSE_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
   if (method == BSE_METHOD_SVD)
     batched_svd_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);

@@ -9,12 +9,30 @@
 // shared memory with a register prefetch of the next tile.
 #include <atomic>
 
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "gemm_tile.cuh"
 #include "kernels.cuh"
 #include "prof.cuh"
 
 static std::atomic<long long> g_launches{0};
 void bse_count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// The dynamic shared-memory limit of a kernel is a per-device attribute: set
+// it once per (device, kernel, size).
+bse_status set_smem_attr(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int>> done;
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(std::make_tuple(dev, func, bytes))) return BSE_OK;
+  BSE_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert(std::make_tuple(dev, func, bytes));
+  return BSE_OK;
+}
 long long bse_total_launches() { return g_launches.load(); }
 
 // Useful (structurally nonzero) multiply-adds of a launch, for the profiler:

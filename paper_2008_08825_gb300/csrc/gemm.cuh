@@ -67,3 +67,5 @@ bse_status gemm_f(cudaStream_t s, const GemmParams<float>& p);
 
 // Launch counter shared by all translation units.
 void bse_count_launch(int64_t k = 1);
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (device, kernel, size)
+bse_status set_smem_attr(const void* func, int bytes);

@@ -348,10 +348,9 @@ __global__ void tr_last_diag(int64_t n, const cplx* A, int64_t lda, double* d, c
 bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const HetrdWork& w,
                        const int64_t* status) {
   if (n <= 0) return BSE_OK;
-  static bool attr = false;
-  if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(tr_hemv_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, HEMV_SMEM));
-    attr = true;
+  {
+    const bse_status r = set_smem_attr((const void*)tr_hemv_strip, HEMV_SMEM);
+    if (r) return r;
   }
   const int64_t ldv = n, ldw = n;
   BSE_CUDA(cudaMemsetAsync(w.V, 0, sizeof(cplx) * n * n, s));

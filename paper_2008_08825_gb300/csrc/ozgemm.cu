@@ -903,11 +903,9 @@ static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_
     bse_internal_set_error("tensor-core GEMM: cuTensorMapEncodeTiled failed");
     return BSE_ERR_CUDA;
   }
-  static bool attr = false;
-  if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(oz_umma_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  UmLayout<S>::SMEM));
-    attr = true;
+  {
+    const bse_status r = set_smem_attr((const void*)oz_umma_kernel<S, T>, UmLayout<S>::SMEM);
+    if (r) return r;
   }
   dim3 grid((unsigned)((ncols_real + UM_BN - 1) / UM_BN), (unsigned)((z.Mp + UM_BM - 1) / UM_BM));
   prof_tc_begin(s);
@@ -951,10 +949,9 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p, double flops
   z.p = p, z.As = As, z.Bs = Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np, z.Kp = Kp;
   if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, cplx>(s, z, Np, flops);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
-  static bool attr = false;
-  if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(oz_mma_kernel<S, cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
+  {
+    const bse_status r = set_smem_attr((const void*)oz_mma_kernel<S, cplx>, smem);
+    if (r) return r;
   }
   dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
   prof_tc_begin(s);
@@ -1006,10 +1003,9 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p, double f
   z.Kp = Kp;
   if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, double>(s, z, Np, flops);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
-  static bool attr = false;
-  if (!attr) {
-    BSE_CUDA(cudaFuncSetAttribute(oz_mma_kernel<S, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
+  {
+    const bse_status r = set_smem_attr((const void*)oz_mma_kernel<S, double>, smem);
+    if (r) return r;
   }
   dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
   prof_tc_begin(s);

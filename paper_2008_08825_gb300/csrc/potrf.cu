@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(cplx* __restrict__ A, i
   }
 }
 
-static bool g_diag_attr_set = false;
 
 int chol_block_size() { return CHOL_NB; }
 size_t chol_linv_elems(int64_t n) { return (size_t)((n + CHOL_NB - 1) / CHOL_NB) * CHOL_NB * CHOL_NB; }
@@ -84,9 +83,9 @@ size_t chol_linv_elems(int64_t n) { return (size_t)((n + CHOL_NB - 1) / CHOL_NB)
 bse_status potrf_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, cplx* Linv, int64_t* status,
                        int64_t err_code) {
   const size_t smem = sizeof(cplx) * 2 * CHOL_NB * DIAG_LD;
-  if (!g_diag_attr_set) {
-    BSE_CUDA(cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    g_diag_attr_set = true;
+  {
+    const bse_status r = set_smem_attr((const void*)potrf_diag_kernel, (int)smem);
+    if (r) return r;
   }
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), mone = mkc(-1.0, 0.0);
   for (int64_t k0 = 0; k0 < n; k0 += CHOL_NB) {
