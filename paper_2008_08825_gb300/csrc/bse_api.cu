@@ -153,6 +153,7 @@ static void carve_chol(Plan& pl, CholBuffers& b, int64_t n, int64_t k, int prec)
   b.h.e = pl.take<double>(n);
   b.h.part = pl.take<cplx>(hetrd_part_elems(n));
   b.h.small = pl.take<cplx>(4 * nbt * nbt + 64);
+  b.h.S2 = pl.take<cplx>((size_t)n * 2 * nbt);
   b.t.carve(pl, n, k);
   b.Z = pl.take<double>((size_t)n * k);
   b.lam = pl.take<double>(k);
@@ -194,6 +195,7 @@ static void carve_svd(Plan& pl, SvdBuffers& b, int64_t n, int64_t k, int prec) {
   b.g.e = pl.take<double>(n);
   b.g.part = pl.take<cplx>(gebrd_part_elems(n));
   b.g.small = pl.take<cplx>(4 * nbt + 64);
+  b.g.S2 = pl.take<cplx>((size_t)n * 2 * nbt);
   b.t.carve(pl, 2 * n, k);
   b.Z = pl.take<double>((size_t)2 * n * k);
   b.UB = pl.take<double>((size_t)n * k);
@@ -237,6 +239,7 @@ static void carve_sqrt(Plan& pl, SqrtBuffers& b, int64_t n, int64_t k, int prec)
   b.h.e = pl.take<double>(n);
   b.h.part = pl.take<cplx>(hetrd_part_elems(n));
   b.h.small = pl.take<cplx>(4 * nbt * nbt + 64);
+  b.h.S2 = pl.take<cplx>((size_t)n * 2 * nbt);
   b.t.carve(pl, n, n);
   b.Z = pl.take<double>((size_t)n * n);
   b.d2 = pl.take<double>(n);
@@ -269,6 +272,7 @@ static void carve_tda(Plan& pl, TdaBuffers& b, int64_t n, int64_t k) {
   b.h.e = pl.take<double>(n);
   b.h.part = pl.take<cplx>(hetrd_part_elems(n));
   b.h.small = pl.take<cplx>(4 * nbt * nbt + 64);
+  b.h.S2 = pl.take<cplx>((size_t)n * 2 * nbt);
   b.t.carve(pl, n, k);
   b.Z = pl.take<double>((size_t)n * k);
   b.lam = pl.take<double>(k);

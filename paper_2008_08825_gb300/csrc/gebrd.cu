@@ -368,7 +368,26 @@ bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const Ge
       BLAUNCH(bd_x_assemble, ceil_div_u(m, AR), a, (int)ceil_div_u(m, BT64));
     }
     const int64_t t0 = p + bs, mt = n - t0;
-    if (mt > 0) {
+    if (mt > 0 && p + 2 * bs <= n) {
+      // A22 -= U_p Y^H + X V_p^H as ONE product of depth 2 bs: [U_p X] [Y V_p]^H,
+      // with X parked in the (still zero) columns p+bs .. p+2bs-1 of U and
+      // [Y V_p] assembled in S2; the parked columns are zeroed again before
+      // the next panel writes its reflectors there
+      cplx* A22 = A + IDX2(t0, t0, lda);
+      const size_t rowb = sizeof(cplx) * (size_t)mt;
+      BSE_CUDA(cudaMemcpy2DAsync(w.U + IDX2(t0, p + bs, ld), sizeof(cplx) * ld, w.X + IDX2(t0, 0, ld),
+                                 sizeof(cplx) * ld, rowb, bs, cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpy2DAsync(w.S2, sizeof(cplx) * n, w.Y + IDX2(t0, 0, ld), sizeof(cplx) * ld, rowb, bs,
+                                 cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpy2DAsync(w.S2 + IDX2(0, bs, n), sizeof(cplx) * n, w.Vr + IDX2(t0, p, ld), sizeof(cplx) * ld,
+                                 rowb, bs, cudaMemcpyDeviceToDevice, s));
+      GemmParams<cplx> g = gemm_params<cplx>(mt, mt, 2 * bs, OPN, w.U + IDX2(t0, p, ld), ld, OPC, w.S2, n, mone, one,
+                                             A22, lda);
+      g.status = status;
+      bse_status r = gemm_z(s, g);
+      if (r) return r;
+      BSE_CUDA(cudaMemset2DAsync(w.U + IDX2(t0, p + bs, ld), sizeof(cplx) * ld, 0, rowb, bs, s));
+    } else if (mt > 0) {
       cplx* A22 = A + IDX2(t0, t0, lda);
       GemmParams<cplx> g1 = gemm_params<cplx>(mt, mt, bs, OPN, w.U + IDX2(t0, p, ld), ld, OPC,
                                               w.Y + IDX2(t0, 0, ld), ld, mone, one, A22, lda);

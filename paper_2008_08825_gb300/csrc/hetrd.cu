@@ -386,7 +386,27 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)ga, status);
     }
     const int64_t t0 = p + bs, mt = n - t0;
-    if (mt > 0) {
+    if (mt > 0 && p + 2 * bs <= n) {
+      // A22 -= V W^H + W V^H as ONE product of depth 2 bs: [W V_p] [V_p W]^H,
+      // with W parked in the (still zero) columns p+bs .. p+2bs-1 of V for the
+      // second operand and [W V_p] assembled in S2; the parked columns are
+      // zeroed again before the next panel writes its reflectors there
+      cplx* A22 = A + IDX2(t0, t0, lda);
+      const size_t rowb = sizeof(cplx) * (size_t)mt;
+      BSE_CUDA(cudaMemcpy2DAsync(w.V + IDX2(t0, p + bs, ldv), sizeof(cplx) * ldv, w.W + IDX2(t0, 0, ldw),
+                                 sizeof(cplx) * ldw, rowb, bs, cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpy2DAsync(w.S2, sizeof(cplx) * n, w.W + IDX2(t0, 0, ldw), sizeof(cplx) * ldw, rowb, bs,
+                                 cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpy2DAsync(w.S2 + IDX2(0, bs, n), sizeof(cplx) * n, w.V + IDX2(t0, p, ldv), sizeof(cplx) * ldv,
+                                 rowb, bs, cudaMemcpyDeviceToDevice, s));
+      GemmParams<cplx> g = gemm_params<cplx>(mt, mt, 2 * bs, OPN, w.S2, n, OPC, w.V + IDX2(t0, p, ldv), ldv, mone,
+                                             one, A22, lda);
+      g.lowerC = 1;
+      g.status = status;
+      bse_status r = gemm_z(s, g);
+      if (r) return r;
+      BSE_CUDA(cudaMemset2DAsync(w.V + IDX2(t0, p + bs, ldv), sizeof(cplx) * ldv, 0, rowb, bs, s));
+    } else if (mt > 0) {
       // A22 -= V W^H + W V^H  (lower triangle of rows/cols >= t0)
       cplx* A22 = A + IDX2(t0, t0, lda);
       GemmParams<cplx> g1 = gemm_params<cplx>(mt, mt, bs, OPN, w.V + IDX2(t0, p, ldv), ldv, OPC,

@@ -53,6 +53,7 @@ struct HetrdWork {
   double* e;      // n  (e[j] = T(j+1, j), j < n-1)
   cplx* part;     // partial-sum scratch, hetrd_part_elems(n)
   cplx* small;    // small scratch (>= 4 * nbt * nbt + 64)
+  cplx* S2;       // n x 2 nbt: one operand of the merged trailing update
 };
 int hetrd_panel();
 // reflectors per block in the back-transformations (T factor of this width)
@@ -105,6 +106,7 @@ struct GebrdWork {
   double* e;      // n
   cplx* part;     // partial-sum scratch
   cplx* small;    // small scratch
+  cplx* S2;       // n x 2 nbt: one operand of the merged trailing update
 };
 size_t gebrd_part_elems(int64_t n);
 bse_status gebrd_upper(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const GebrdWork& w,
