@@ -55,12 +55,17 @@ static int split_layers(int64_t tiles) {
   }
   return best;
 }
-constexpr int HR = 8;      // row tiles per CTA of the strip matvec
+constexpr int HR = 8;      // at most this many row tiles per CTA of the strip matvec
 // partial-sum slots of the matvec: one per 64-wide column strip (row
-// products) plus one per chunk of HR row tiles (column products)
+// products) plus one per chunk of row tiles (column products; at most nt)
 static inline int64_t hemv_slots(int64_t n) {
   const int64_t nt = (n + 63) / 64;
-  return nt + (nt + HR - 1) / HR;
+  return 2 * nt;
+}
+// row tiles per CTA: up to HR, fewer while that leaves under ~2 CTAs per SM
+static inline int hemv_chunk(int64_t nt) {
+  const int64_t c = nt * nt / 608;
+  return c < 1 ? 1 : (c > HR ? HR : (int)c);
 }
 size_t hetrd_part_elems(int64_t n) {
   return (size_t)(hemv_slots(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64;
@@ -170,7 +175,8 @@ constexpr int HT = 64;
 constexpr int HEMV_SMEM = (int)sizeof(cplx) * HT * (HT + 1);  // 66,560 bytes of dynamic shared memory
 
 // Column strips: CTA (ch, bj) takes the row tiles
-// bi in [bj + ch HR, min(nt, bj + (ch+1) HR)) of the 64-wide column strip bj.
+// bi in [bj + ch hr, min(nt, bj + (ch+1) hr)) of the 64-wide column strip bj
+// (hr = hemv_chunk(nt)).
 // Thread (row r, column eighth q) reads 8 entries of its row per tile; the
 // row products of a tile go to slot bj (one writer per row), the column
 // products accumulate in registers over the CTA's tiles and, after one
@@ -181,8 +187,9 @@ constexpr int HEMV_SMEM = (int)sizeof(cplx) * HT * (HT + 1);  // 66,560 bytes of
 // s1 = W^H v and s2 = V_panel^H v (over rows >= j+1) beside the matvec.
 __global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
                                                      const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
-                                                     int64_t ldpart, int64_t p, int jj, const cplx* __restrict__ W,
-                                                     int64_t ldw, cplx* __restrict__ s12, const int64_t* status) {
+                                                     int64_t ldpart, int hr, int64_t p, int jj,
+                                                     const cplx* __restrict__ W, int64_t ldw, cplx* __restrict__ s12,
+                                                     const int64_t* status) {
   extern __shared__ cplx T[];  // column partials, T[c * (HT + 1) + r]
   __shared__ cplx vc[HT];
   __shared__ cplx rs[8][HT];
@@ -202,9 +209,9 @@ __global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const
     }
     return;
   }
-  const int64_t bj = blockIdx.y, bi0 = bj + (int64_t)blockIdx.x * HR;
+  const int64_t bj = blockIdx.y, bi0 = bj + (int64_t)blockIdx.x * hr;
   if (bj >= nt || bi0 >= nt) return;
-  const int64_t bi1 = bi0 + HR < nt ? bi0 + HR : nt;
+  const int64_t bi1 = bi0 + hr < nt ? bi0 + hr : nt;
   const int64_t c0 = bj * HT;
   const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;  // row, column eighth
   if (tid < HT) vc[tid] = (c0 + tid < m) ? V[IDX2(base + c0 + tid, j, ldv)] : mkc(0.0, 0.0);
@@ -267,7 +274,7 @@ constexpr int AR = 64;
 
 __global__ void __launch_bounds__(256) tr_w_assemble(int64_t n, int64_t p, int64_t j, const cplx* __restrict__ V,
                                                      int64_t ldv, cplx* __restrict__ W, int64_t ldw,
-                                                     const cplx* __restrict__ part, int64_t ldpart, int nch,
+                                                     const cplx* __restrict__ part, int64_t ldpart, int nch, int hr,
                                                      const cplx* __restrict__ s12, const cplx* __restrict__ tau,
                                                      double* __restrict__ dpart, const int64_t* status) {
   __shared__ cplx s1[NBT], s2[NBT];
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(256) tr_w_assemble(int64_t n, int64_t p, int64
   if (r < m) {
     // row products of strips 0..b, column products of the chunks of strip b
     const int b = (int)(r / HT);
-    const int nchk = (nch - b + HR - 1) / HR;
+    const int nchk = (nch - b + hr - 1) / hr;
     for (int c = qq; c <= b; c += 4) y = cadd(y, part[r + c * ldpart]);
     for (int c = qq; c < nchk; c += 4) y = cadd(y, part[r + (nch + c) * ldpart]);
     const int64_t gr = base + r;
@@ -373,16 +380,18 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       {
         prof_launch_begin(s);
         const int jj = (int)(j - p);
-        const dim3 hg((unsigned)((nt + HR - 1) / HR), (unsigned)(nt + (jj > 0 ? 1 : 0)));
-        tr_hemv_strip<<<hg, 512, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, p, jj, w.W, ldw, s12, status);
+        const int hr = hemv_chunk(nt);
+        const dim3 hg((unsigned)((nt + hr - 1) / hr), (unsigned)(nt + (jj > 0 ? 1 : 0)));
+        tr_hemv_strip<<<hg, 512, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, hr, p, jj, w.W, ldw, s12,
+                                                 status);
         prof_launch_end(s, "tr_hemv_strip");
         bse_count_launch();
         BSE_LAUNCH_CHECK();
       }
       const int64_t nch = nt;
       const unsigned ga = ceil_div_u(m, AR);
-      LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, s12, w.tau, dpart,
-             status);
+      LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, hemv_chunk(nt), s12, w.tau,
+             dpart, status);
       LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)ga, status);
     }
     const int64_t t0 = p + bs, mt = n - t0;
