@@ -101,7 +101,16 @@ typedef enum {
    * bulk-tensor copies; 1: warp-level mma.sync (the earlier engine, kept for
    * comparison).  Both give the same FP32 level sums exactly (the combined
    * set of levels >= 7 up to its rounding). */
-  BSE_OPT_TC_ENGINE = 3
+  BSE_OPT_TC_ENGINE = 3,
+  /* Mixed form, tcgen05 engine: limit, in SM clock cycles, of each wait of
+   * its pipeline (copy landed, stage free, accumulators ready).  0 (default)
+   * means 2e9 cycles, about 1 s.  When a wait runs out the product stops
+   * issuing, lets the copies and MMAs it started finish (those waits keep
+   * the default limit, so nothing is left in flight), frees its TMEM and
+   * records BSE_ERR_TIMEOUT; the solve then returns BSE_ERR_TIMEOUT and
+   * writes no output.  A tiny value forces that path (a test uses it); the
+   * handle stays usable. */
+  BSE_OPT_TC_WAIT_CYCLES = 4
 } bse_option;
 bse_status bse_set_option(bse_handle h, int option, int64_t value);
 
@@ -299,10 +308,15 @@ int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
  * computes what bse_solve_chol computes with il = 1, iu = k (Alg. 2, the
  * lowest k pairs), with one thread block on one SM, and allocates nothing:
  * no device or pinned memory, no handle, no host heap.  Its workspace is a
- * fixed __device__ array of BSE_NOALLOC_SCRATCH_BYTES, created with the
- * library's module on each device that uses it.
+ * fixed __device__ array of BSE_NOALLOC_SCRATCH_BYTES that exists once the
+ * CUDA module holding it is loaded on the device.  Under CUDA's default lazy
+ * module loading that load happens inside the first call on each device,
+ * and it is the one point where device memory is taken (the scratch plus the
+ * modules' code): make the first call at start-up, before another allocator
+ * claims the memory.  A call with n == 0 does this set-up and solves nothing.
  * n        1 <= n <= BSE_NOALLOC_MAX_N; larger n returns BSE_ERR_TOO_LARGE
- *          without launching anything; n == 0 or k == 0 returns BSE_OK.
+ *          without launching anything; n == 0 (set-up only) or k == 0
+ *          returns BSE_OK.
  * k        0 <= k <= n.
  * A, B     device, n x n Hermitian, leading dimension n (packed), lower
  *          triangle read.
@@ -311,8 +325,9 @@ int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
  * info     host, may be NULL: info->info = failing 1-based column for the
  *          not-positive-definite codes, else 0.
  * stream   work is enqueued on it, then the stream is synchronised.
- * Set-up: the first call with a device current looks up the scratch address
- * for that device; make that first call before any stream capture on it.
+ * Set-up: the first call with a device current loads the modules, looks up
+ * the scratch address for that device and sets the kernel's attributes;
+ * make that first call before any stream capture on it.
  * Calls that overlap on one device share the scratch and race: serialise
  * them.  This entry point reports through its return code only; it does not
  * update bse_last_error().

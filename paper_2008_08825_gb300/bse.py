@@ -152,6 +152,11 @@ class Handle:
         """Mixed form: 'tcgen05' (default; TMEM accumulators, TMA) or 'mma_sync'."""
         _check(lib().bse_set_option(self._h, 3, {"tcgen05": 0, "mma_sync": 1}[engine]))
 
+    def set_tc_wait_cycles(self, value: int) -> None:
+        """Mixed form, tcgen05 engine: limit of its pipeline waits in clock
+        cycles (0 restores the default, about 1 s)."""
+        _check(lib().bse_set_option(self._h, 4, int(value)))
+
     def set_batch_ctas_per_sm(self, value: int) -> None:
         """Batched solves: 1 or 2 resident CTAs per SM for the persistent kernel."""
         _check(lib().bse_set_option(self._h, 2, int(value)))
@@ -247,6 +252,8 @@ def solve_noalloc(A: torch.Tensor, B: torch.Tensor, k: int, omega: torch.Tensor,
     complex128 contiguous (Xt.mT is X).  This wrapper allocates nothing on the
     device either.  Raises BseError on a nonzero status.
     '''
+    if A.dim() != 2 or A.shape[0] != A.shape[1] or tuple(B.shape) != tuple(A.shape):
+        raise TypeError("bse: A and B must both be n x n")
     n = int(A.shape[0])
     for T in (A, B):
         if T.dtype != torch.complex128 or not T.is_cuda or not _is_colmajor(T):
@@ -256,10 +263,13 @@ def solve_noalloc(A: torch.Tensor, B: torch.Tensor, k: int, omega: torch.Tensor,
     for T in (Xt, Yt):
         if T.dtype != torch.complex128 or tuple(T.shape) != (k, n) or not T.is_contiguous():
             raise TypeError("bse: Xt, Yt must be contiguous complex128 tensors of shape (k, n)")
+    if any(T.device != A.device for T in (B, omega, Xt, Yt)):
+        raise TypeError("bse: A, B, omega, Xt and Yt must be on one device")
     info = _Info()
-    code = lib().bse_solve_chol_noalloc(n, int(k), _P(A.data_ptr()), _P(B.data_ptr()), _P(omega.data_ptr()),
-                                        _P(Xt.data_ptr()), _P(Yt.data_ptr()), ctypes.byref(info),
-                                        _P(_stream_ptr(stream)))
+    with torch.cuda.device(A.device):
+        code = lib().bse_solve_chol_noalloc(n, int(k), _P(A.data_ptr()), _P(B.data_ptr()), _P(omega.data_ptr()),
+                                            _P(Xt.data_ptr()), _P(Yt.data_ptr()), ctypes.byref(info),
+                                            _P(_stream_ptr(stream)))
     if code != OK:
         msg = (f"n = {n} above the allocation-free limit {NOALLOC_MAX_N}" if code == 10
                else "allocation-free solve failed")

@@ -51,6 +51,7 @@ struct bse_context {
   int sms = 0;
   int64_t oz_min = (int64_t)1 << 24;
   int oz_engine = OZ_ENGINE_TCGEN05;
+  int64_t oz_wait = 0;  // 0: the engine's default wait limit
   int batch_cps = 1;
 };
 
@@ -73,7 +74,7 @@ struct ProfGuard {
 // Makes the tensor-core product workspace current for one solve (mixed form).
 struct OzGuard {
   explicit OzGuard(const OzWork& w) { oz_set_current(w); }
-  ~OzGuard() { oz_set_current(OzWork{nullptr, 0, 0, OZ_ENGINE_TCGEN05}); }
+  ~OzGuard() { oz_set_current(OzWork{nullptr, 0, 0, OZ_ENGINE_TCGEN05, 0}); }
 };
 
 // ---------------------------------------------------------------------------
@@ -391,7 +392,7 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
   Plan pl(ws);
   CholBuffers b;
   carve_chol(pl, b, n, k, prec);
-  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min, h->oz_engine});
+  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min, h->oz_engine, h->oz_wait});
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
@@ -472,7 +473,7 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
   Plan pl(ws);
   SvdBuffers b;
   carve_svd(pl, b, n, k, prec);
-  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min, h->oz_engine});
+  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min, h->oz_engine, h->oz_wait});
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
@@ -563,7 +564,7 @@ static bse_status solve_sqrt_dev(bse_context* h, int64_t n, const cplx* A, int64
   Plan pl(ws);
   SqrtBuffers b;
   carve_sqrt(pl, b, n, k, prec);
-  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min, h->oz_engine});
+  OzGuard ozg(OzWork{b.oz, b.oz ? oz_work_bytes(n, 8) : 0, h->oz_min, h->oz_engine, h->oz_wait});
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
@@ -947,6 +948,12 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value) {
   if (option == BSE_OPT_TC_ENGINE) {
     if (value != 0 && value != 1) return bse_internal_set_error("BSE_OPT_TC_ENGINE must be 0 or 1"), BSE_ERR_ARG;
     h->oz_engine = (int)value;
+    return BSE_OK;
+  }
+  if (option == BSE_OPT_TC_WAIT_CYCLES) {
+    if (value < 0 || value > ((int64_t)1 << 36))
+      return bse_internal_set_error("BSE_OPT_TC_WAIT_CYCLES must be in [0, 2^36]"), BSE_ERR_ARG;
+    h->oz_wait = value;
     return BSE_OK;
   }
   if (option == BSE_OPT_BATCH_CTAS_PER_SM) {

@@ -16,6 +16,7 @@
 // HBM (n'^2 complex MACs over n'^2 * 16 bytes needs 3.4 TFLOP/s to saturate
 // 6.8 TB/s; the part delivers 1.2), so the one-stage reduction does the same
 // FP64 work as a band reduction and saves its second back-transformation.
+#include <atomic>
 #include <cmath>
 
 #include "kernels.cuh"
@@ -36,14 +37,20 @@ size_t backtransform_tmp_elems(int64_t k) {
 // Split-K layers for a product whose tiles do not fill the GPU: the count
 // s <= WSPLIT that brings tiles * s closest to whole waves of 2 CTAs per SM.
 static int split_layers(int64_t tiles) {
-  static int slots = 0;
+  // 2 CTA slots per SM of the current device (looked up once per device)
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> slots_of[kMaxDev];
+  int dev = 0, slots = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError(), dev = -1;
+  if (dev >= 0 && dev < kMaxDev) slots = slots_of[dev].load(std::memory_order_relaxed);
   if (!slots) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    int sms = 0;
+    if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
       cudaGetLastError();
-      sms = 148;
+      sms = 152;  // GB300
     }
     slots = 2 * sms;
+    if (dev >= 0 && dev < kMaxDev) slots_of[dev].store(slots, std::memory_order_relaxed);
   }
   if (tiles >= 4 * slots) return 1;
   int best = 1;

@@ -141,6 +141,7 @@ struct OzWork {
   size_t bytes;
   int64_t min_mnk;  // products with m*n*k below this stay on the DFMA engine
   int engine;       // OZ_ENGINE_TCGEN05 (TMEM accumulators, TMA) or OZ_ENGINE_MMA_SYNC
+  int64_t wait_cycles;  // tcgen05 engine: limit of its pipeline waits in clock cycles (0: default, ~1 s)
 };
 void oz_set_current(const OzWork& w);
 OzWork oz_current();

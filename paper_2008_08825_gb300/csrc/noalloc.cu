@@ -7,7 +7,13 @@
 //     lock and cudaFree would synchronise the whole device;
 //   - services that must not meet an out-of-memory error after start-up.
 // All of its device memory is one file-scope __device__ array (the scratch
-// below), created with the module; the host side uses fixed-size locals.
+// below); the host side uses fixed-size locals.  The array exists once this
+// file's CUDA module is loaded on a device.  Under CUDA's default lazy module
+// loading, the cudaGetSymbolAddress of the first call on a device is what
+// loads it (and the solver kernel's module loads at its first launch), so the
+// first call is the one that takes device memory: the 8 MiB scratch and the
+// code.  Callers make it at start-up, before another allocator claims the
+// memory; a call with n == 0 does only this set-up.
 //
 // Set-up, once per device: the first call made with a device current looks
 // up the scratch's device address for that device (cudaGetSymbolAddress) and
@@ -69,10 +75,11 @@ extern "C" bse_status bse_solve_chol_noalloc(int64_t n, int64_t k, const double*
   }
   if (n < 0 || k < 0 || k > n) return BSE_ERR_ARG;
   if (n > kMaxN) return BSE_ERR_TOO_LARGE;
-  if (n == 0 || k == 0) return BSE_OK;
+  void* base = nullptr;
+  if (n == 0) return scratch_for_current_device(&base);  // set-up only
+  if (k == 0) return BSE_OK;
   if (!A || !B || !omega || !X || !Y) return BSE_ERR_ARG;
   if (kStatusBytes + batched_inst_bytes(n, k) > kScratchBytes) return BSE_ERR_TOO_LARGE;
-  void* base = nullptr;
   const bse_status r = scratch_for_current_device(&base);
   if (r) return r;
   cudaStream_t s = (cudaStream_t)stream;

@@ -216,6 +216,7 @@ struct OzArgs {
   const int* ea;
   const int* fb;
   int64_t Mp, Np, Kp;
+  long long wait;  // tcgen05 engine: limit of its pipeline waits (cycles)
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
@@ -455,7 +456,7 @@ constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 32, UM_STAGES = 2;
 constexpr int UM_SLICE_A = UM_BM * UM_BK * 2, UM_SLICE_B = UM_BN * UM_BK * 2;  // 8 KB, 4 KB
 constexpr int UM_FOLD = 512 / UM_BK;  // k-tiles per fold (512 k', the exactness bound)
 constexpr int UM_ROWB = UM_BK * 2;    // bytes per k-major tile row
-constexpr long long UM_WAIT_CYCLES = 2000000000LL;                               // about 1 s
+constexpr long long UM_WAIT_CYCLES = 2000000000LL;  // default wait limit, about 1 s; drains always use it
 
 template <int S>
 struct UmLayout {
@@ -469,7 +470,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 // bounded wait on an mbarrier phase; false on timeout (which sets the abort
 // flag) or, when abort_flag is given, as soon as another role has aborted
 __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                        volatile int* timeout_flag) {
+                                        volatile int* timeout_flag, long long limit) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t ok;
@@ -480,7 +481,7 @@ __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity, volatile 
         : "memory");
     if (ok) return true;
     if (abort_flag && *abort_flag) return false;
-    if (clock64() - t0 > UM_WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       *timeout_flag = 1;
       return false;
     }
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     // producer
     for (int kt = 0; kt < ntile; ++kt, ++issued) {
       const int st = kt % UM_STAGES;
-      if (kt >= UM_STAGES && !um_wait(empty0 + 8 * st, ((kt / UM_STAGES) - 1) & 1, ab, ab)) break;
+      if (kt >= UM_STAGES && !um_wait(empty0 + 8 * st, ((kt / UM_STAGES) - 1) & 1, ab, ab, z.wait)) break;
       const uint32_t fb = full0 + 8 * st;
       const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
       const int x = (int)(kb2 + (int64_t)kt * UM_BK);
@@ -596,10 +597,10 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     for (int kt = 0; kt < ntile && ok; ++kt) {
       const int st = kt % UM_STAGES;
       if (kt % UM_FOLD == 0) {  // the sets are zero (initially, or read and cleared by the last fold)
-        ok = um_wait(tempty, (kt / UM_FOLD) & 1, ab, ab);
+        ok = um_wait(tempty, (kt / UM_FOLD) & 1, ab, ab, z.wait);
         if (!ok) break;
       }
-      ok = um_wait(full0 + 8 * st, (kt / UM_STAGES) & 1, ab, ab);
+      ok = um_wait(full0 + 8 * st, (kt / UM_STAGES) & 1, ab, ab, z.wait);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
@@ -639,13 +640,13 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     // input) marks its column, which ends as NaN.
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const int col0 = ((warp - 4) >> 2) * EC;
-    const uint32_t z = 0;
+    const uint32_t zero = 0;
     auto clear_sets = [&](int c0) {
 #pragma unroll
       for (int set = 0; set < UM_NSETS; ++set)
         asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(
                          tmem + lane_base + set * UM_BN + col0 + c0),
-                     "r"(z));
+                     "r"(zero));
     };
     if (nfold > 0) {
 #pragma unroll
@@ -656,7 +657,7 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty) : "memory");
     }
     for (int f = 0; f < nfold; ++f) {
-      if (!um_wait(tfull, f & 1, ab, ab)) break;
+      if (!um_wait(tfull, f & 1, ab, ab, z.wait)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int c0 = 0; c0 < EC; c0 += 4) {
@@ -704,12 +705,12 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     // every MMA this thread issued has completed once `drain` flips (bounded)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(drain)
                  : "memory");
-    um_wait(drain, 0, nullptr, ab);
+    um_wait(drain, 0, nullptr, ab, UM_WAIT_CYCLES);
   }
   if (failed && warp == 0 && lane == 0) {
     // the copies still in flight land before the CTA leaves (bounded)
     for (int kt = issued - UM_STAGES < 0 ? 0 : issued - UM_STAGES; kt < issued; ++kt)
-      um_wait(full0 + 8 * (kt % UM_STAGES), (kt / UM_STAGES) & 1, nullptr, ab);
+      um_wait(full0 + 8 * (kt % UM_STAGES), (kt / UM_STAGES) & 1, nullptr, ab, UM_WAIT_CYCLES);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -851,7 +852,7 @@ __global__ void oz_split_d_kernel(int64_t R, int64_t C, const double* X, int64_t
 }  // namespace
 
 // Workspace (thread-current, set by the solve entry points)
-static thread_local OzWork g_oz = {nullptr, 0, 0, OZ_ENGINE_TCGEN05};
+static thread_local OzWork g_oz = {nullptr, 0, 0, OZ_ENGINE_TCGEN05, 0};
 void oz_set_current(const OzWork& w) { g_oz = w; }
 OzWork oz_current() { return g_oz; }
 
@@ -947,6 +948,7 @@ static bse_status oz_run(cudaStream_t s, const GemmParams<cplx>& p, double flops
   BSE_LAUNCH_CHECK();
   OzArgs<cplx> z;
   z.p = p, z.As = As, z.Bs = Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np, z.Kp = Kp;
+  z.wait = g_oz.wait_cycles > 0 ? (long long)g_oz.wait_cycles : UM_WAIT_CYCLES;
   if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, cplx>(s, z, Np, flops);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   {
@@ -1001,6 +1003,7 @@ static bse_status oz_run_d(cudaStream_t s, const GemmParams<double>& p, double f
   OzArgs<double> z;
   z.p = p, z.As = (const uint32_t*)As, z.Bs = (const uint32_t*)Bs, z.ea = ea, z.fb = fb, z.Mp = Mp, z.Np = Np,
   z.Kp = Kp;
+  z.wait = g_oz.wait_cycles > 0 ? (long long)g_oz.wait_cycles : UM_WAIT_CYCLES;
   if (g_oz.engine == OZ_ENGINE_TCGEN05) return umma_launch<S, double>(s, z, Np, flops);
   const int smem = 2 * 2 * S * OZ_BM * OZ_ROWB;
   {

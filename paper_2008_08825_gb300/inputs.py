@@ -98,21 +98,39 @@ def _hermitian_full(M: np.ndarray) -> np.ndarray:
     return L + L.conj().T + np.diag(np.real(np.diag(M)))
 
 
-def kappa_sweep(n: int, kappa: float, seed: int = 0, iters: int = 60, power_iters: int = 200):
-    """Base workload with kappa(A - B) set to `kappa`; returns (A, B, achieved_kappa_estimate).
+def _rank_one(u: np.ndarray, s: float) -> np.ndarray:
+    """s u u^H built from real element-wise products and sums, one rounding
+    each, so that the same u and s give the same bits on every platform (a
+    complex multiply may be fused differently by different numpy builds)."""
+    ur, ui = np.ascontiguousarray(u.real), np.ascontiguousarray(u.imag)
+    P = np.empty((u.size, u.size), dtype=np.complex128, order="F")
+    P.real = (np.multiply.outer(ur, ur) + np.multiply.outer(ui, ui)) * s
+    P.imag = (np.multiply.outer(ui, ur) - np.multiply.outer(ur, ui)) * s
+    return P
 
-    The lowest eigenpair (mu, u) of A - B comes from inverse iteration with a
-    library (LAPACK, through scipy) Cholesky solve, and mu_max from power
-    iteration; both are input construction, not part of the solver.
-    """
-    import scipy.linalg as sla
 
+def _kappa_base(n: int, seed: int):
     rng = np.random.default_rng(seed)
     d = rng.uniform(1.0, 10.0, n)
     d[np.argmin(d)] = 0.5
     A = np.asfortranarray(_hermitian_gaussian(rng, n) * 0.1)
     A[np.diag_indices(n)] += d
     B = np.asfortranarray(_hermitian_gaussian(rng, n) * 0.05)
+    return A, B, rng
+
+
+def kappa_shift(n: int, kappa: float, seed: int = 0, iters: int = 60, power_iters: int = 200):
+    """The rank-one shift of ``kappa_sweep``: (u, c, achieved_kappa_estimate).
+
+    The lowest eigenpair (mu, u) of A - B comes from inverse iteration with a
+    library (LAPACK, through scipy) Cholesky solve, and mu_max from power
+    iteration; both are input construction, not part of the solver.  Their
+    last bits depend on the platform's LAPACK and BLAS, so a result that must
+    be reproduced elsewhere stores (u, c) and passes them back as ``shift``.
+    """
+    import scipy.linalg as sla
+
+    A, B, rng = _kappa_base(n, seed)
     M2 = A - B
     cf = sla.cho_factor(M2, lower=True, check_finite=False)
     u = np.ones(n, dtype=np.complex128) / np.sqrt(n)
@@ -127,10 +145,24 @@ def kappa_sweep(n: int, kappa: float, seed: int = 0, iters: int = 60, power_iter
         v /= np.linalg.norm(v)
     mu_max = float(np.real(np.vdot(v, M2 @ v)))
     c = mu - mu_max / kappa
-    P = np.outer(u, u.conj()) * (0.5 * c)
-    A = np.asfortranarray(A - P)
-    B = np.asfortranarray(B + P)
-    return A, B, mu_max / (mu - c)
+    return u, c, mu_max / (mu - c)
+
+
+def kappa_sweep(n: int, kappa: float, seed: int = 0, iters: int = 60, power_iters: int = 200, shift=None):
+    """Base workload with kappa(A - B) set to `kappa`; returns (A, B, achieved_kappa_estimate).
+
+    ``shift`` = (u, c) from an earlier ``kappa_shift`` call reproduces that
+    call's matrices bit for bit on any platform (the estimate is then None).
+    """
+    if shift is None:
+        u, c, est = kappa_shift(n, kappa, seed, iters, power_iters)
+    else:
+        (u, c), est = shift, None
+    A, B, _ = _kappa_base(n, seed)
+    P = _rank_one(np.asarray(u, dtype=np.complex128), 0.5 * float(c))
+    A -= P
+    B += P
+    return A, B, est
 
 
 def batched_sizes(count: int = 512, seed: int = 10_000, lo: int = 32, hi: int = 1024) -> np.ndarray:

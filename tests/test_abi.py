@@ -65,11 +65,13 @@ def test_workspace_sizes_per_method(lib):
 def test_noalloc_host_checks_need_no_gpu(lib):
     """Argument checks of the allocation-free entry point run before any CUDA
     call: n above the limit gives BSE_ERR_TOO_LARGE, bad k an argument error,
-    n = 0 success; none of them touches a device."""
+    k = 0 success; none of them touches a device.  n = 0 is the set-up call,
+    which needs a device: without one it reports BSE_ERR_CUDA."""
     lib.bse_solve_chol_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 7
     lib.bse_solve_chol_noalloc.restype = ctypes.c_int
     assert lib.bse_solve_chol_noalloc(bse.NOALLOC_MAX_N + 1, 1, None, None, None, None, None, None, None) == 10
     assert lib.bse_solve_chol_noalloc(8, 9, None, None, None, None, None, None, None) == 1
     assert lib.bse_solve_chol_noalloc(8, -1, None, None, None, None, None, None, None) == 1
-    assert lib.bse_solve_chol_noalloc(0, 0, None, None, None, None, None, None, None) == 0
+    assert lib.bse_solve_chol_noalloc(8, 0, None, None, None, None, None, None, None) == 0
+    assert lib.bse_solve_chol_noalloc(0, 0, None, None, None, None, None, None, None) == 7
     assert lib.bse_solve_chol_noalloc(8, 2, None, None, None, None, None, None, None) == 1  # NULL pointers

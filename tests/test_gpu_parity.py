@@ -495,6 +495,32 @@ def test_mixed_kappa_sweep(kappa, method, dev, tc_handle):
     print(f"mixed kappa={kappa:g} {method}: rel.err(smallest)={abs(om[0] - om_r[0]) / om_r[0]:.2e}")
 
 
+def test_tc_wait_limit_timeout_path(dev):
+    """The tcgen05 engine's pipeline waits are bounded.  With a limit of one
+    clock cycle they run out: the product stops issuing, drains the copies and
+    MMAs it started (those waits keep the default limit), frees its TMEM and
+    records BSE_ERR_TIMEOUT, which the solve returns without writing output.
+    The same handle at the default limit then solves correctly."""
+    n = 129
+    A, B = _base(n, n)
+    om_r, _, _ = _oracle(n, n)
+    h = bse.Handle()
+    h.set_tc_min_mnk(1)
+    with pytest.raises(bse.BseError) as e:
+        h.set_tc_wait_cycles(-1)
+    assert e.value.code == 1
+    h.set_tc_wait_cycles(1)
+    for method in ("chol", "svd"):
+        with pytest.raises(bse.BseError) as e:
+            _gpu(A, B, method, dev, precision="mixed", handle=h)
+        assert e.value.code == 6, e.value
+    h.set_tc_wait_cycles(0)
+    for method in ("chol", "svd"):
+        om, X, Y = _gpu(A, B, method, dev, precision="mixed", handle=h)
+        assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+        assert sigma_residual(X, Y) <= 1e-10
+
+
 @pytest.mark.parametrize("n", [1, 63, 130, 257])
 @pytest.mark.parametrize("method", METHODS)
 def test_mixed_tc_engines_agree(n, method, dev):
