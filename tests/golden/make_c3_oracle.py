@@ -13,7 +13,7 @@ One file per case, ``c3_n<n>_seed<seed>_<case>.npz``, holding:
             (the shift itself comes from LAPACK and is platform dependent)
   sha256    hash of A and B (complex128, column-major bytes): the test checks
             that it rebuilt exactly the matrices the oracle saw
-  seconds, threads, sweeps-free metadata for the record
+  seconds, threads, machine   metadata for the record
 
 Usage (hours at n = 8192 on a few cores; each case is written when done):
     python tests/golden/make_c3_oracle.py --n 8192 --cases base,1e2,1e6,1e10
@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import os
+import platform
 import sys
 import time
 
@@ -81,7 +82,8 @@ def main():
         omega, _, _ = oracle.solve_svd(A, B, vectors=False)
         dt = time.time() - t0
         np.savez(out, omega=omega, sha256=np.array(digest), n=np.int64(args.n), seed=np.int64(args.seed),
-                 case=np.array(case), seconds=np.float64(dt), threads=np.int64(oracle.get_threads()), **extra)
+                 case=np.array(case), seconds=np.float64(dt), threads=np.int64(oracle.get_threads()),
+                 machine=np.array(platform.machine()), **extra)
         print(f"{case}: n={args.n} {dt:.0f} s, omega[0]={omega[0]:.17g} -> {os.path.basename(out)}", flush=True)
 
 

@@ -1,10 +1,13 @@
 """The stored full-size accuracy values (tests/golden/c3_*.npz) are what the
 committed script writes: for the small copies (n = 256) the inputs rebuilt
-from the generator and the stored shift hash to the stored digest, and the
-oracle, run again, gives the stored omega bit for bit (the oracle's results do
-not depend on its thread count)."""
+from the generator and the stored shift hash to the stored digest on any
+host, and the oracle, run again, gives the stored omega bit for bit on the
+kind of machine that wrote them (its results do not depend on its thread
+count).  On another architecture the C library's elementary functions may
+round differently, so there the oracle agrees to rounding level only."""
 import glob
 import os
+import platform
 import sys
 
 import numpy as np
@@ -33,7 +36,12 @@ def test_small_golden_reproduces(path):
     A, B, _ = mk.build_inputs(n, seed, case, shift=shift)
     assert mk.input_hash(A, B) == str(z["sha256"])
     om, _, _ = oracle.solve_svd(A, B, vectors=False)
-    assert np.array_equal(om, z["omega"])
+    ref = z["omega"]
+    made_on = str(z["machine"]) if "machine" in z.files else "x86_64"
+    if platform.machine() == made_on:
+        assert np.array_equal(om, ref)
+    else:
+        assert np.max(np.abs(om - ref)) <= 1e-13 * ref.max()
 
 
 def test_golden_cases_present():
