@@ -34,24 +34,27 @@ size_t backtransform_tmp_elems(int64_t k) {
   return (size_t)(2 + GSPLIT) * BTB * BTB + (2 + WSPLIT) * (size_t)BTB * k;
 }
 
-// Split-K layers for a product whose tiles do not fill the GPU: the count
-// s <= WSPLIT that brings tiles * s closest to whole waves of 2 CTAs per SM.
-static int split_layers(int64_t tiles) {
-  // 2 CTA slots per SM of the current device (looked up once per device)
+// SM count of the current device (looked up once per device)
+static int device_sms() {
   constexpr int kMaxDev = 64;
-  static std::atomic<int> slots_of[kMaxDev];
-  int dev = 0, slots = 0;
+  static std::atomic<int> sms_of[kMaxDev];
+  int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError(), dev = -1;
-  if (dev >= 0 && dev < kMaxDev) slots = slots_of[dev].load(std::memory_order_relaxed);
-  if (!slots) {
-    int sms = 0;
+  if (dev >= 0 && dev < kMaxDev) sms = sms_of[dev].load(std::memory_order_relaxed);
+  if (!sms) {
     if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
       cudaGetLastError();
       sms = 152;  // GB300
     }
-    slots = 2 * sms;
-    if (dev >= 0 && dev < kMaxDev) slots_of[dev].store(slots, std::memory_order_relaxed);
+    if (dev >= 0 && dev < kMaxDev) sms_of[dev].store(sms, std::memory_order_relaxed);
   }
+  return sms;
+}
+
+// Split-K layers for a product whose tiles do not fill the GPU: the count
+// s <= WSPLIT that brings tiles * s closest to whole waves of 2 CTAs per SM.
+static int split_layers(int64_t tiles) {
+  const int slots = 2 * device_sms();
   if (tiles >= 4 * slots) return 1;
   int best = 1;
   double best_eff = 0.0;
@@ -63,19 +66,23 @@ static int split_layers(int64_t tiles) {
   return best;
 }
 constexpr int HR = 8;      // at most this many row tiles per CTA of the strip matvec
-// partial-sum slots of the matvec: one per 64-wide column strip (row
-// products) plus one per chunk of row tiles (column products; at most nt)
+// partial-sum slots of the matvec: one per 32-wide column strip (row
+// products) plus one per chunk of row tiles (column products; at most one
+// per strip)
 static inline int64_t hemv_slots(int64_t n) {
-  const int64_t nt = (n + 63) / 64;
-  return 2 * nt;
+  const int64_t nst = (n + 31) / 32;
+  return 2 * nst;
 }
-// row tiles per CTA: up to HR, fewer while that leaves under ~2 CTAs per SM
-static inline int hemv_chunk(int64_t nt) {
-  const int64_t c = nt * nt / 608;
+// row tiles (64 x 32) per work item: up to HR, fewer while that leaves under
+// ~4 items per CTA (ntr^2 tiles in all, two CTAs per SM)
+static inline int hemv_chunk(int64_t ntr) {
+  const int64_t c = ntr * ntr / 1216;
   return c < 1 ? 1 : (c > HR ? HR : (int)c);
 }
 size_t hetrd_part_elems(int64_t n) {
-  return (size_t)(hemv_slots(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64;
+  // partial-sum slots, norm and dot partials, and the matvec's per-column
+  // work-queue counters (n ints)
+  return (size_t)(hemv_slots(n) + 2) * (size_t)(n + 1) + 4 * (n / RB + 2) + 4 * NBT + 64 + (size_t)(n / 4 + 4);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -175,37 +182,57 @@ __global__ void __launch_bounds__(RB) tr_house(int64_t n, int64_t j, const cplx*
   if (r < n) V[IDX2(r, j, ldv)] = (r == j + 1) ? mkc(1.0, 0.0) : cmul(A[IDX2(r, j, lda)], hs.scal);
 }
 
-// 3. y = A22 v from the lower triangle in 64 x 64 tiles: each tile is read
-// once and gives both its row sums (A v) and, off the diagonal, its column
-// sums (A^H v).
-constexpr int HT = 64;
-constexpr int HEMV_SMEM = (int)sizeof(cplx) * HT * (HT + 1);  // 66,560 bytes of dynamic shared memory
+// 3. y = A22 v from the lower triangle in tiles of 64 rows x 32 columns:
+// each tile is read once and gives both its row sums (A v) and, below the
+// diagonal, its column sums (A^H v).
+constexpr int HT = 64;            // rows per tile
+constexpr int HS = 32;            // columns per tile (strip width)
+constexpr int HEMV_THREADS = 256;  // two CTAs per SM
+// dynamic shared memory: two prefetch stages of one tile (each thread's 8
+// entries, [u][thread]), the column-partial transpose T[32][65] and the
+// double-buffered row partials rs[2][4][64]
+constexpr int HEMV_STAGE = 8 * HEMV_THREADS;  // complex entries per stage
+constexpr int HEMV_SMEM = (int)sizeof(cplx) * (2 * HEMV_STAGE + HS * (HT + 1) + 2 * 4 * HT);  // 107,008 bytes
 
-// Column strips: CTA (ch, bj) takes the row tiles
-// bi in [bj + ch hr, min(nt, bj + (ch+1) hr)) of the 64-wide column strip bj
-// (hr = hemv_chunk(nt)).
-// Thread (row r, column eighth q) reads 8 entries of its row per tile; the
-// row products of a tile go to slot bj (one writer per row), the column
-// products accumulate in registers over the CTA's tiles and, after one
-// shared-memory reduction, go to slot nt + ch.  Per entry: two complex
-// multiply-adds and no shared-memory staging (a tile-per-CTA form that
-// staged every column product ran at 64% of the DFMA rate).
-// With jj > 0 an extra row of CTAs (blockIdx.y == nt) computes the panel dots
-// s1 = W^H v and s2 = V_panel^H v (over rows >= j+1) beside the matvec.
-__global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda,
-                                                     const cplx* __restrict__ V, int64_t ldv, cplx* __restrict__ part,
-                                                     int64_t ldpart, int hr, int64_t p, int jj,
-                                                     const cplx* __restrict__ W, int64_t ldw, cplx* __restrict__ s12,
-                                                     const int64_t* status) {
-  extern __shared__ cplx T[];  // column partials, T[c * (HT + 1) + r]
-  __shared__ cplx vc[HT];
-  __shared__ cplx rs[8][HT];
+__device__ __forceinline__ void hemv_cp16(uint32_t dst, const void* src, bool in) {
+  // 16-byte copy to shared memory, L2 only; zero fill when `in` is false
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
+}
+
+// Work items: column strip bj (32 columns) and chunk ch of its row tiles,
+// bi in [bj/2 + ch hr, min(ntr, bj/2 + (ch+1) hr)), hr = hemv_chunk(ntr); items
+// are numbered strip by strip, so the longest come first and the last ones
+// are the short strips near the end of the matrix.  The grid is two CTAs per
+// SM (plus the dot CTAs) and each CTA takes items from a per-column counter
+// until none is left, which balances the triangular work across the SMs.
+// Thread (row r, column quarter q) handles 8 entries of its row per tile; the
+// tile after the current one is prefetched with cp.async into shared memory
+// (each thread copies, and later reads, only its own 8 entries, so the
+// prefetch needs no barrier).  The row products of a tile go to slot bj (one
+// writer per row, double-buffered so one barrier per tile suffices); the
+// column products accumulate in registers over the item's tiles and, after
+// one shared-memory reduction, go to slot nst + ch.  Per entry: two complex
+// multiply-adds.  (Two CTAs of 8 warps per SM keep the FP64 pipe busier
+// than one CTA of 16 warps with 64-wide strips.)
+// The first `ndots` CTAs compute the panel dots s1 = W^H v and
+// s2 = V_panel^H v (over rows >= j+1) beside the matvec (jj > 0).
+__global__ void __launch_bounds__(HEMV_THREADS, 2)
+    tr_hemv_strip(int64_t n, int64_t j, const cplx* __restrict__ A, int64_t lda, const cplx* __restrict__ V,
+                  int64_t ldv, cplx* __restrict__ part, int64_t ldpart, int hr, int64_t p, int jj,
+                  const cplx* __restrict__ W, int64_t ldw, cplx* __restrict__ s12, int ndots, int* __restrict__ counter,
+                  const int64_t* status) {
+  extern __shared__ __align__(16) unsigned char hsm[];
+  cplx* stage = (cplx*)hsm;              // [2][8][HEMV_THREADS]
+  cplx* T = stage + 2 * HEMV_STAGE;       // column partials, T[c * (HT + 1) + r]
+  cplx* rs = T + HS * (HT + 1);           // [2][4][HT]
+  __shared__ cplx vc[HS];
   __shared__ double red[32];
+  __shared__ int item_s[2];  // strip, chunk of the CTA's current item
   if (*(volatile const int64_t*)status) return;
   const int64_t base = j + 1, m = n - base;
-  const int64_t nt = (m + HT - 1) / HT;
-  if (jj > 0 && (int64_t)blockIdx.y == nt) {
-    for (int d = blockIdx.x; d < 2 * jj; d += gridDim.x) {
+  const int nst = (int)((m + HS - 1) / HS), ntr = (int)((m + HT - 1) / HT);
+  if ((int)blockIdx.x < ndots) {
+    for (int d = blockIdx.x; d < 2 * jj; d += ndots) {
       const int q = d % jj, which = d / jj;  // which 0: W, 1: V
       const cplx* col = which == 0 ? W + IDX2(0, q, ldw) : V + IDX2(0, p + q, ldv);
       cplx acc = mkc(0.0, 0.0);
@@ -216,62 +243,97 @@ __global__ void __launch_bounds__(512) tr_hemv_strip(int64_t n, int64_t j, const
     }
     return;
   }
-  const int64_t bj = blockIdx.y, bi0 = bj + (int64_t)blockIdx.x * hr;
-  if (bj >= nt || bi0 >= nt) return;
-  const int64_t bi1 = bi0 + hr < nt ? bi0 + hr : nt;
-  const int64_t c0 = bj * HT;
-  const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;  // row, column eighth
-  if (tid < HT) vc[tid] = (c0 + tid < m) ? V[IDX2(base + c0 + tid, j, ldv)] : mkc(0.0, 0.0);
-  __syncthreads();
-  cplx colacc[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) colacc[u] = mkc(0.0, 0.0);
-  for (int64_t bi = bi0; bi < bi1; ++bi) {
-    const int64_t r0 = bi * HT, gr = r0 + r;
-    const bool diag = bi == bj;
-    const cplx vrr = gr < m ? V[IDX2(base + gr, j, ldv)] : mkc(0.0, 0.0);
-    const cplx* Ar = A + IDX2(base + gr, base + c0, lda);
-    cplx av[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = q * 8 + u;
-      const bool in = gr < m && c0 + c < m && (!diag || r >= c);
-      av[u] = in ? __ldg(Ar + (int64_t)c * lda) : mkc(0.0, 0.0);
-    }
-    cplx rowacc = mkc(0.0, 0.0);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = q * 8 + u;
-      cfma(rowacc, av[u], vc[c]);
-      if (!diag || r > c) cfma_cj(colacc[u], av[u], vrr);
-    }
-    rs[q][r] = rowacc;
-    __syncthreads();
-    if (tid < HT && r0 + tid < m) {
-      cplx y = rs[0][tid];
-#pragma unroll
-      for (int e = 1; e < 8; ++e) y = cadd(y, rs[e][tid]);
-      part[r0 + tid + bj * ldpart] = y;
+  const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;  // row, column quarter
+  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
+  int cur_b = 0, cur_acc = 0;  // thread 0's decode cursor: items come in increasing order
+  for (;;) {
+    if (tid == 0) {
+      // decode the next item (one thread, 32-bit arithmetic), continuing the
+      // scan over the strips from the previous item
+      const int item = atomicAdd(counter, 1);
+      int c = 0;
+      for (; cur_b < nst; ++cur_b) {
+        const int nc = (ntr - (cur_b >> 1) + hr - 1) / hr;
+        if (item < cur_acc + nc) {
+          c = item - cur_acc;
+          break;
+        }
+        cur_acc += nc;
+      }
+      item_s[0] = cur_b;
+      item_s[1] = c;
     }
     __syncthreads();
-  }
+    const int bj = item_s[0], ch = item_s[1];
+    if (bj >= nst) break;  // uniform: every thread reads the same item
+    const int bi0 = (bj >> 1) + ch * hr, bi1 = bi0 + hr < ntr ? bi0 + hr : ntr;
+    const int64_t c0 = (int64_t)bj * HS;
+    auto prefetch = [&](int bi, int st) {
+      const int64_t gr = (int64_t)bi * HT + r;
+      const cplx* Ar = A + IDX2(base + gr, base + c0, lda);
 #pragma unroll
-  for (int u = 0; u < 8; ++u) T[(q * 8 + u) * (HT + 1) + r] = colacc[u];
-  __syncthreads();
-  {
-    // column c: thread (c, eighth q) adds rows q*8 .. q*8+7, then the 8 eighths
-    const int c = tid & 63;
-    cplx acc = mkc(0.0, 0.0);
+      for (int u = 0; u < 8; ++u) {
+        const int64_t gc = c0 + q * 8 + u;
+        const bool in = gr < m && gc < m && gr >= gc;
+        hemv_cp16(stage_s + (uint32_t)sizeof(cplx) * (st * HEMV_STAGE + u * HEMV_THREADS + tid),
+                  in ? (const void*)(Ar + (int64_t)(q * 8 + u) * lda) : (const void*)A, in);
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    if (tid < HS) vc[tid] = (c0 + tid < m) ? V[IDX2(base + c0 + tid, j, ldv)] : mkc(0.0, 0.0);
+    prefetch(bi0, 0);
+    __syncthreads();
+    cplx colacc[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc = cadd(acc, T[c * (HT + 1) + q * 8 + u]);
-    rs[q][c] = acc;
-  }
-  __syncthreads();
-  if (tid < HT && c0 + tid < m) {
-    cplx y = rs[0][tid];
+    for (int u = 0; u < 8; ++u) colacc[u] = mkc(0.0, 0.0);
+    int t = 0;
+    for (int bi = bi0; bi < bi1; ++bi, ++t) {
+      if (bi + 1 < bi1) {
+        prefetch(bi + 1, (t + 1) & 1);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+      const int64_t r0 = (int64_t)bi * HT, gr = r0 + r;
+      const cplx vrr = gr < m ? V[IDX2(base + gr, j, ldv)] : mkc(0.0, 0.0);
+      const cplx* sb = stage + (t & 1) * HEMV_STAGE + tid;
+      cplx av[8];
 #pragma unroll
-    for (int e = 1; e < 8; ++e) y = cadd(y, rs[e][tid]);
-    part[c0 + tid + (nt + blockIdx.x) * ldpart] = y;
+      for (int u = 0; u < 8; ++u) av[u] = sb[u * HEMV_THREADS];
+      cplx ra0 = mkc(0.0, 0.0), ra1 = mkc(0.0, 0.0);  // two chains of row products
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = q * 8 + u;
+        cfma((u & 1) ? ra1 : ra0, av[u], vc[c]);
+        if (gr > c0 + c) cfma_cj(colacc[u], av[u], vrr);
+      }
+      cplx* rsb = rs + (t & 1) * 4 * HT;
+      rsb[q * HT + r] = cadd(ra0, ra1);
+      __syncthreads();
+      if (tid < HT && r0 + tid < m) {
+        const cplx y = cadd(cadd(rsb[tid], rsb[HT + tid]), cadd(rsb[2 * HT + tid], rsb[3 * HT + tid]));
+        part[r0 + tid + (int64_t)bj * ldpart] = y;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) T[(q * 8 + u) * (HT + 1) + r] = colacc[u];
+    __syncthreads();
+    {
+      // column c: thread (c, eighth e) adds rows e*8 .. e*8+7, then the 8 eighths
+      const int c = tid & 31, e = tid >> 5;
+      cplx acc = mkc(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = cadd(acc, T[c * (HT + 1) + e * 8 + u]);
+      rs[e * HS + c] = acc;
+    }
+    __syncthreads();
+    if (tid < HS && c0 + tid < m) {
+      cplx y = rs[tid];
+#pragma unroll
+      for (int e = 1; e < 8; ++e) y = cadd(y, rs[e * HS + tid]);
+      part[c0 + tid + (int64_t)(nst + ch) * ldpart] = y;
+    }
+    __syncthreads();
   }
 }
 
@@ -299,10 +361,14 @@ __global__ void __launch_bounds__(256) tr_w_assemble(int64_t n, int64_t p, int64
   const int64_t r = (int64_t)blockIdx.x * AR + rl;
   cplx y = mkc(0.0, 0.0);
   if (r < m) {
-    // row products of strips 0..b, column products of the chunks of strip b
-    const int b = (int)(r / HT);
-    const int nchk = (nch - b + hr - 1) / hr;
-    for (int c = qq; c <= b; c += 4) y = cadd(y, part[r + c * ldpart]);
+    // row products of the strips 0 .. 2 bi + 1 that meet row tile bi, column
+    // products of the chunks of the row's own strip b (nch strips, their
+    // row tiles in chunks of hr)
+    const int bi = (int)(r / HT), b = (int)(r / HS);
+    const int ntr = (nch + 1) / 2;
+    const int last = 2 * bi + 1 < nch - 1 ? 2 * bi + 1 : nch - 1;
+    const int nchk = (ntr - (b >> 1) + hr - 1) / hr;
+    for (int c = qq; c <= last; c += 4) y = cadd(y, part[r + c * ldpart]);
     for (int c = qq; c < nchk; c += 4) y = cadd(y, part[r + (nch + c) * ldpart]);
     const int64_t gr = base + r;
     for (int q = qq; q < jj; q += 4) {
@@ -373,6 +439,9 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
   const int64_t slots = hemv_slots(n);
   double* npart = (double*)(w.part + slots * ldpart);
   double* dpart = npart + (n / RB + 2);
+  int* counters = (int*)(dpart + 2 * (n / AR + 4));  // one work-queue counter per column
+  BSE_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * n, s));
+  const int64_t sms = device_sms();
   cplx* s12 = w.small;
   const cplx one = mkc(1.0, 0.0), mone = mkc(-1.0, 0.0);
   for (int64_t p = 0; p < n - 1; p += NBT) {
@@ -383,22 +452,24 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       LAUNCH(tr_col_update, g1, RB, n, p, j, A, lda, w.V, ldv, w.W, ldw, w.d, npart, status);
       const unsigned g2 = ceil_div_u(m, RB);
       LAUNCH(tr_house, g2, RB, n, j, A, lda, w.V, ldv, w.tau, w.e, npart, (int)g1, status);
-      const int64_t nt = (m + HT - 1) / HT;  // tile rows; partial slots
+      const int64_t nst = (m + HS - 1) / HS, ntr = (m + HT - 1) / HT;  // strips, row tiles
+      const int hr = hemv_chunk(ntr);
       {
         prof_launch_begin(s);
         const int jj = (int)(j - p);
-        const int hr = hemv_chunk(nt);
-        const dim3 hg((unsigned)((nt + hr - 1) / hr), (unsigned)(nt + (jj > 0 ? 1 : 0)));
-        tr_hemv_strip<<<hg, 512, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, hr, p, jj, w.W, ldw, s12,
-                                                 status);
+        int64_t nitems = 0;
+        for (int64_t bj = 0; bj < nst; ++bj) nitems += (ntr - bj / 2 + hr - 1) / hr;
+        const int ndots = jj > 0 ? (2 * jj < 16 ? 2 * jj : 16) : 0;
+        const unsigned hg = (unsigned)(ndots + (nitems < 2 * sms ? nitems : 2 * sms));
+        tr_hemv_strip<<<hg, HEMV_THREADS, HEMV_SMEM, s>>>(n, j, A, lda, w.V, ldv, part, ldpart, hr, p, jj, w.W, ldw,
+                                                           s12, ndots, counters + j, status);
         prof_launch_end(s, "tr_hemv_strip");
         bse_count_launch();
         BSE_LAUNCH_CHECK();
       }
-      const int64_t nch = nt;
       const unsigned ga = ceil_div_u(m, AR);
-      LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nch, hemv_chunk(nt), s12, w.tau,
-             dpart, status);
+      LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nst, hr, s12, w.tau, dpart,
+             status);
       LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)ga, status);
     }
     const int64_t t0 = p + bs, mt = n - t0;
