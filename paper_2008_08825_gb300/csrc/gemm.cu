@@ -113,9 +113,16 @@ static bse_status gemm_launch(cudaStream_t s, const GemmParams<T>& p) {
   return BSE_OK;
 }
 
+// split-K on the tensor-core engine: tcgen05 only, plain epilogue, beta 0
+template <typename T>
+static bool oz_split_ok(const OzWork& oz, const GemmParams<T>& p) {
+  return p.kchunk == 0 ||
+         (oz.engine == OZ_ENGINE_TCGEN05 && p.kchunk % 64 == 0 && !beta_nz(p.beta) && p.epi == EPI_NONE);
+}
+
 bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
   const OzWork oz = oz_current();
-  if (oz.ptr && p.kchunk == 0 && p.opA != OPT && p.opB != OPT && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
+  if (oz.ptr && oz_split_ok(oz, p) && p.opA != OPT && p.opB != OPT && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
     const bool prof = prof_current() != nullptr;
     if (prof) prof_gemm_begin(s);
     const double flops = useful_macs(p) * 8.0;
@@ -127,7 +134,7 @@ bse_status gemm_z(cudaStream_t s, const GemmParams<cplx>& p) {
 }
 bse_status gemm_d(cudaStream_t s, const GemmParams<double>& p) {
   const OzWork oz = oz_current();
-  if (oz.ptr && p.kchunk == 0 && p.opA != OPC && p.opB != OPC && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
+  if (oz.ptr && oz_split_ok(oz, p) && p.opA != OPC && p.opB != OPC && (double)p.m * p.n * p.k >= (double)oz.min_mnk) {
     const bool prof = prof_current() != nullptr;
     if (prof) prof_gemm_begin(s);
     const double flops = useful_macs(p) * 2.0;

@@ -52,9 +52,8 @@ static int device_sms() {
 }
 
 // Split-K layers for a product whose tiles do not fill the GPU: the count
-// s <= WSPLIT that brings tiles * s closest to whole waves of 2 CTAs per SM.
-static int split_layers(int64_t tiles) {
-  const int slots = 2 * device_sms();
+// s <= WSPLIT that brings tiles * s closest to whole waves of `slots` CTAs.
+static int split_layers(int64_t tiles, int slots) {
   if (tiles >= 4 * slots) return 1;
   int best = 1;
   double best_eff = 0.0;
@@ -578,11 +577,14 @@ bse_status apply_block_reflector(cudaStream_t s, int64_t n, int64_t k, const cpl
   BSE_LAUNCH_CHECK();
   GemmParams<cplx> p1 = gemm_params<cplx>(bs, k, m, OPC, Vp, ldvb, OPN, Vout + r0, ldv, one, zero, W1, bs);
   p1.status = status;
-  // W1 = V^H Z has (bs/64) x (k/64) tiles of depth m; on the DFMA engine
-  // (the tensor-core engine keeps its own tiling) split k for whole waves
+  // W1 = V^H Z is a thin output of depth m: split k so that the tiles fill
+  // whole waves -- (bs/64) x (k/64) tiles over 2 CTAs per SM on the DFMA
+  // engine, (bs/128) x (2k/64) tiles over the persistent tensor-core
+  // engine's one CTA per SM
   const OzWork oz = oz_current();
-  const bool on_tc = oz.ptr && (double)bs * k * m >= (double)oz.min_mnk;
-  const int ws = on_tc ? 1 : split_layers(((bs + 63) / 64) * ((k + 63) / 64));
+  const bool on_tc = oz.ptr && oz.engine == OZ_ENGINE_TCGEN05 && (double)bs * k * m >= (double)oz.min_mnk;
+  const int ws = on_tc ? split_layers(((bs + 127) / 128) * ((2 * k + 63) / 64), device_sms())
+                       : split_layers(((bs + 63) / 64) * ((k + 63) / 64), 2 * device_sms());
   if (ws > 1 && m >= 64 * ws) {
     cplx* Wl = Gl + (size_t)GSPLIT * bs * bs;  // ws layers of bs x k
     p1.C = Wl;

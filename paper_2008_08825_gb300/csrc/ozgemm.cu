@@ -25,6 +25,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 #include "prof.cuh"
 
@@ -216,7 +218,8 @@ struct OzArgs {
   const int* ea;
   const int* fb;
   int64_t Mp, Np, Kp;
-  long long wait;  // tcgen05 engine: limit of its pipeline waits (cycles)
+  long long wait;       // tcgen05 engine: limit of its pipeline waits (cycles)
+  int64_t ncols_real;   // tcgen05 engine: real output columns (a multiple of 64)
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
@@ -503,33 +506,61 @@ __host__ __device__ constexpr uint32_t um_idesc(int n) {
 }
 constexpr int UM_NSETS = 7;  // levels 2..6, then two sets for the levels >= 7
 
+// Geometry of one output tile of the persistent kernel (all roles compute it
+// the same way from the linear tile index L): 128 real rows x 64 real
+// columns, grouped rasterisation in bands of 8 tile rows, and with split-K
+// (p.kchunk > 0) layer tz = L / (tiles per layer) of the k range.
+struct UmTile {
+  int64_t i0, jr0, jc0, kb2, tz;
+  int ntile, nfold;
+  bool valid;
+};
+
+template <typename T>
+__device__ __forceinline__ UmTile um_tile(const GemmParams<T>& p, int64_t L, int64_t ntx, int64_t nty) {
+  constexpr int XF = sizeof(T) == sizeof(cplx) ? 2 : 1;
+  UmTile t;
+  const int64_t per = ntx * nty;
+  t.tz = L / per;
+  const int64_t lin = L - t.tz * per;
+  const int64_t grp = lin / (8 * ntx), first = grp * 8;
+  const int64_t rows = (nty - first) < 8 ? (nty - first) : 8;
+  const int64_t loc = lin % (8 * ntx);
+  const int64_t ty = first + loc % rows, tx = loc / rows;
+  t.i0 = ty * UM_BM, t.jr0 = tx * UM_BN, t.jc0 = t.jr0 / XF;
+  t.valid = t.i0 < p.m && t.jc0 < p.n && !(p.lowerC && t.jc0 > t.i0 + UM_BM - 1);
+  int64_t kb = 0, ke = p.k;
+  if (p.triA == TRI_LO) ke = min(ke, t.i0 + UM_BM);
+  if (p.triA == TRI_UP) kb = max(kb, t.i0);
+  if (p.triB == TRI_LO) kb = max(kb, t.jc0);
+  if (p.triB == TRI_UP) ke = min(ke, t.jc0 + UM_BN / XF);
+  if (p.kchunk > 0) kb = max(kb, t.tz * p.kchunk), ke = min(ke, (t.tz + 1) * p.kchunk);
+  t.kb2 = (XF * kb / UM_BK) * UM_BK;
+  const int64_t ke2 = XF * ke;
+  t.ntile = ke2 > t.kb2 ? (int)((ke2 - t.kb2 + UM_BK - 1) / UM_BK) : 0;
+  t.nfold = (t.ntile + UM_FOLD - 1) / UM_FOLD;
+  return t;
+}
+
+// Persistent form: one CTA per SM walks the tiles L = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  The stage ring, the MMA issue and the folds
+// run on global counters across tiles, so the producer streams the next
+// tile's slices while the current one finishes, and the fold warps write a
+// tile's result (from registers, after its last fold has cleared the TMEM
+// sets) while the MMAs of the next tile already run.
+constexpr int UM_FOLD_WARPS = 16;                       // warps 4 .. 19
+constexpr int UM_THREADS = 32 * (4 + UM_FOLD_WARPS);    // 640
 template <int S, typename T>
-__global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, const __grid_constant__ CUtensorMap tmA,
-                                                          const __grid_constant__ CUtensorMap tmB) {
+__global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> z,
+                                                                 const __grid_constant__ CUtensorMap tmA,
+                                                                 const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ __align__(1024) unsigned char usm[];
   using L = UmLayout<S>;
   constexpr bool CPLX = sizeof(T) == sizeof(cplx);
-  constexpr int XF = CPLX ? 2 : 1;
   const GemmParams<T>& p = z.p;
-  // grouped rasterisation, as in oz_mma_kernel
-  const int64_t gx = gridDim.x, gy = gridDim.y;
-  const int64_t lin = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gx;
-  const int64_t grp = lin / (8 * gx), first = grp * 8;
-  const int64_t rows = (gy - first) < 8 ? (gy - first) : 8;
-  const int64_t loc = lin % (8 * gx);
-  const int64_t ty = first + loc % rows, tx = loc / rows;
-  const int64_t i0 = ty * UM_BM, jr0 = tx * UM_BN, jc0 = jr0 / XF;
-  if (i0 >= p.m || jc0 >= p.n) return;
-  if (p.lowerC && jc0 > i0 + UM_BM - 1) return;
   if (p.status && *(volatile const int64_t*)p.status) return;
-  int64_t kb = 0, ke = p.k;
-  if (p.triA == TRI_LO) ke = min(ke, i0 + UM_BM);
-  if (p.triA == TRI_UP) kb = max(kb, i0);
-  if (p.triB == TRI_LO) kb = max(kb, jc0);
-  if (p.triB == TRI_UP) ke = min(ke, jc0 + UM_BN / XF);
-  const int64_t kb2 = (XF * kb / UM_BK) * UM_BK, ke2 = XF * ke;
-  const int ntile = ke2 > kb2 ? (int)((ke2 - kb2 + UM_BK - 1) / UM_BK) : 0;
-  const int nfold = (ntile + UM_FOLD - 1) / UM_FOLD;
+  const int64_t ntx = (z.ncols_real + UM_BN - 1) / UM_BN, nty = (z.Mp + UM_BM - 1) / UM_BM;
+  const int64_t ntiles = ntx * nty * (p.kchunk > 0 ? (p.k + p.kchunk - 1) / p.kchunk : 1);
 
   unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(base + UM_STAGES * L::STAGE);  // full[S] empty[S] tfull tempty drain
@@ -545,7 +576,7 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty0 + 8 * q));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(tempty));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(tempty), "r"(UM_FOLD_WARPS));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(drain));
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -560,75 +591,80 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
   const uint32_t tmem = *tslot;
   volatile int* ab = abort_flag;
 
-  constexpr int EC = UM_BN / 2;  // columns per epilogue thread
-  // a column's value = hi 2^-28 + lo 2^-45 in units of the level-2 products;
-  // after each fold lo keeps only the remainder 0 <= lo < 2^17 (its multiples
-  // of 2^17 move into hi exactly), so it stays a 32-bit integer
-  int64_t hi[EC];
-  int32_t lo[EC];
-#pragma unroll
-  for (int q = 0; q < EC; ++q) hi[q] = 0, lo[q] = 0;
-  uint32_t nanmask = 0;
-
-  int issued = 0;  // producer: loads issued
+  uint32_t issued = 0;  // producer: loads issued (global over the CTA's tiles)
   if (warp == 0 && lane == 0) {
     // producer
-    for (int kt = 0; kt < ntile; ++kt, ++issued) {
-      const int st = kt % UM_STAGES;
-      if (kt >= UM_STAGES && !um_wait(empty0 + 8 * st, ((kt / UM_STAGES) - 1) & 1, ab, ab, z.wait)) break;
-      const uint32_t fb = full0 + 8 * st;
-      const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
-      const int x = (int)(kb2 + (int64_t)kt * UM_BK);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(L::STAGE) : "memory");
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-          "[%5];\n" ::"r"(da),
-          "l"(&tmA), "r"(x), "r"((int)i0), "r"(0), "r"(fb)
-          : "memory");
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-          "[%5];\n" ::"r"(db),
-          "l"(&tmB), "r"(x), "r"((int)jr0), "r"(0), "r"(fb)
-          : "memory");
+    bool ok = true;
+    for (int64_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
+      const UmTile t = um_tile(p, Lt, ntx, nty);
+      if (!t.valid) continue;
+      for (int kt = 0; kt < t.ntile; ++kt, ++issued) {
+        const uint32_t st = issued % UM_STAGES;
+        if (issued >= UM_STAGES && !um_wait(empty0 + 8 * st, ((issued / UM_STAGES) - 1) & 1, ab, ab, z.wait)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = full0 + 8 * st;
+        const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
+        const int x = (int)(t.kb2 + (int64_t)kt * UM_BK);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(L::STAGE) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];\n" ::"r"(da),
+            "l"(&tmA), "r"(x), "r"((int)t.i0), "r"(0), "r"(fb)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];\n" ::"r"(db),
+            "l"(&tmB), "r"(x), "r"((int)t.jr0), "r"(0), "r"(fb)
+            : "memory");
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     bool ok = true;
-    for (int kt = 0; kt < ntile && ok; ++kt) {
-      const int st = kt % UM_STAGES;
-      if (kt % UM_FOLD == 0) {  // the sets are zero (initially, or read and cleared by the last fold)
-        ok = um_wait(tempty, (kt / UM_FOLD) & 1, ab, ab, z.wait);
+    uint32_t g = 0, F = 0;  // k-tiles consumed, folds issued (global)
+    for (int64_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
+      const UmTile t = um_tile(p, Lt, ntx, nty);
+      if (!t.valid) continue;
+      for (int kt = 0; kt < t.ntile; ++kt, ++g) {
+        const uint32_t st = g % UM_STAGES;
+        if (kt % UM_FOLD == 0) {  // the sets are zero (initially, or read and cleared by the last fold)
+          ok = um_wait(tempty, F & 1, ab, ab, z.wait);
+          if (!ok) break;
+        }
+        ok = um_wait(full0 + 8 * st, (g / UM_STAGES) & 1, ab, ab, z.wait);
         if (!ok) break;
-      }
-      ok = um_wait(full0 + 8 * st, (kt / UM_STAGES) & 1, ab, ab, z.wait);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t da = smem_u32(base + st * L::STAGE), db = da + L::A_BYTES;
 #pragma unroll
-      for (int ks = 0; ks < UM_BK / 16; ++ks) {
+        for (int ks = 0; ks < UM_BK / 16; ++ks) {
 #pragma unroll
-        for (int t = 0; t < S; ++t) {
-          const uint64_t ad = um_desc(da + t * UM_SLICE_A + ks * 32);
+          for (int ts = 0; ts < S; ++ts) {
+            const uint64_t ad = um_desc(da + ts * UM_SLICE_A + ks * 32);
 #pragma unroll
-          for (int u = 0; u < S - t; u += 2) {
-            // pair (t, u) [+ (t, u + 1)]: level t + u (0-based) -> column min(t + u, 5) * 64
-            const int lev = t + u;
-            const uint32_t col = (uint32_t)((lev < 5 ? lev : 5) * UM_BN);
-            const uint64_t bd = um_desc(db + u * UM_SLICE_B + ks * 32);
-            const uint32_t idesc = (u + 1 < S - t) ? um_idesc(2 * UM_BN) : um_idesc(UM_BN);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + col),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(1u));
+            for (int u = 0; u < S - ts; u += 2) {
+              // pair (ts, u) [+ (ts, u + 1)]: level ts + u (0-based) -> column min(ts + u, 5) * 64
+              const int lev = ts + u;
+              const uint32_t col = (uint32_t)((lev < 5 ? lev : 5) * UM_BN);
+              const uint64_t bd = um_desc(db + u * UM_SLICE_B + ks * 32);
+              const uint32_t idesc = (u + 1 < S - ts) ? um_idesc(2 * UM_BN) : um_idesc(UM_BN);
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + col),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(1u));
+            }
           }
         }
-      }
-      if (!ok) break;
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty0 + 8 * st)
-                   : "memory");
-      if ((kt + 1) % UM_FOLD == 0 || kt + 1 == ntile)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(tfull)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         empty0 + 8 * st)
                      : "memory");
+        if ((kt + 1) % UM_FOLD == 0 || kt + 1 == t.ntile) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(tfull)
+                       : "memory");
+          ++F;
+        }
+      }
     }
   } else if (warp >= 4) {
     // folds, all in integers: per column, levels 2..6 are exact FP32
@@ -637,7 +673,11 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     // >= 7 round to units of 2^-45, i.e. 2^-59 of the largest product (an
     // integer part at 2^-38 plus the rounded remainder, below 2^35 per fold).
     // No FP64 work until the epilogue.  A non-finite level sum (non-finite
-    // input) marks its column, which ends as NaN.
+    // input) marks its column, which ends as NaN.  Every fold clears the sets
+    // it read, so the next tile's MMAs start from zero.  16 fold warps: warp w
+    // reads TMEM lanes 32 (w % 4) .. + 31 (the quarter its SM sub-partition may
+    // access) and 16 of the 64 columns of every set.
+    constexpr int EC = UM_BN / 4;  // columns per fold/epilogue thread
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const int col0 = ((warp - 4) >> 2) * EC;
     const uint32_t zero = 0;
@@ -648,54 +688,124 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
                          tmem + lane_base + set * UM_BN + col0 + c0),
                      "r"(zero));
     };
-    if (nfold > 0) {
-#pragma unroll
-      for (int c0 = 0; c0 < EC; c0 += 8) clear_sets(c0);
+    auto release_sets = [&]() {
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty) : "memory");
-    }
-    for (int f = 0; f < nfold; ++f) {
-      if (!um_wait(tfull, f & 1, ab, ab, z.wait)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    };
 #pragma unroll
-      for (int c0 = 0; c0 < EC; c0 += 4) {
-        int64_t tot[4], low[4];
+    for (int c0 = 0; c0 < EC; c0 += 8) clear_sets(c0);
+    release_sets();
+    uint32_t F = 0;  // folds consumed (global)
+    bool ok = true;
+    for (int64_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
+      const UmTile t = um_tile(p, Lt, ntx, nty);
+      if (!t.valid) continue;
+      // a column's value = hi 2^-28 + lo 2^-45 in units of the level-2
+      // products; after each fold lo keeps only the remainder 0 <= lo < 2^17
+      // (its multiples of 2^17 move into hi exactly), so it stays 32-bit
+      int64_t hi[EC];
+      int32_t lo[EC];
 #pragma unroll
-        for (int set = 0; set < UM_NSETS; ++set) {
-          uint32_t v[4];
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                       : "r"(tmem + lane_base + set * UM_BN + col0 + c0));
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      for (int q = 0; q < EC; ++q) hi[q] = 0, lo[q] = 0;
+      uint32_t nanmask = 0;
+      for (int f = 0; f < t.nfold; ++f, ++F) {
+        const bool got = um_wait(tfull, F & 1, ab, ab, z.wait);
+        if (!__all_sync(0xffffffffu, got)) {  // warp-uniform: the loads below are .sync.aligned
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float x = __uint_as_float(v[q]);
-            if (set < 5) {
-              const int iv = __float2int_rn(x * (float)(1 << (7 * set)));  // exact
-              tot[q] = set == 0 ? (int64_t)iv : tot[q] * 128 + iv;
-            } else {
-              if (!(fabsf(x) <= 3.0e38f)) nanmask |= 1u << (c0 + q);
-              const float y = x * 274877906944.0f;  // 2^38, exact
-              const float yi = rintf(y);
-              const int64_t iv = (int64_t)(int)yi * 128 + __float2int_rn((y - yi) * 128.0f);  // units 2^-45
-              low[q] = set == 5 ? iv : low[q] + iv;
+        for (int c0 = 0; c0 < EC; c0 += 4) {
+          int64_t tot[4], low[4];
+#pragma unroll
+          for (int set = 0; set < UM_NSETS; ++set) {
+            uint32_t v[4];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                         : "r"(tmem + lane_base + set * UM_BN + col0 + c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float x = __uint_as_float(v[q]);
+              if (set < 5) {
+                const int iv = __float2int_rn(x * (float)(1 << (7 * set)));  // exact
+                tot[q] = set == 0 ? (int64_t)iv : tot[q] * 128 + iv;
+              } else {
+                if (!(fabsf(x) <= 3.0e38f)) nanmask |= 1u << (c0 + q);
+                const float y = x * 274877906944.0f;  // 2^38, exact
+                const float yi = rintf(y);
+                const int64_t iv = (int64_t)(int)yi * 128 + __float2int_rn((y - yi) * 128.0f);  // units 2^-45
+                low[q] = set == 5 ? iv : low[q] + iv;
+              }
             }
           }
-        }
-        if (f + 1 < nfold && (c0 & 7) == 4) clear_sets(c0 - 4);
+          if ((c0 & 7) == 4) clear_sets(c0 - 4);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t l = (int64_t)lo[c0 + q] + low[q];
-          hi[c0 + q] += tot[q] + (l >> 17);
-          lo[c0 + q] = (int32_t)(l & 0x1FFFF);
+          for (int q = 0; q < 4; ++q) {
+            const int64_t l = (int64_t)lo[c0 + q] + low[q];
+            hi[c0 + q] += tot[q] + (l >> 17);
+            lo[c0 + q] = (int32_t)(l & 0x1FFFF);
+          }
+        }
+        release_sets();
+      }
+      if (!ok) break;
+      // epilogue: thread = one row of the tile and columns [col0, col0 + 32)
+      // of its 64 real columns; complex -- real columns (2j, 2j+1) are (Re,
+      // Im) of logical column jc0 + col0/2 + j; real -- column jc0 + col0 + q
+      const int64_t i = t.i0 + (warp & 3) * 32 + lane;
+      if (i >= p.m) continue;
+      T* C = p.C + (p.kchunk > 0 ? t.tz * p.cstride : 0);
+      const int ei = z.ea[i];
+      const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+      auto value = [&](int q, int sc) -> double {
+        if ((nanmask >> q) & 1u) return qnan;
+        return ldexp((double)hi[q], sc - 28) + ldexp((double)lo[q], sc - 45);
+      };
+      if constexpr (CPLX) {
+        const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
+#pragma unroll
+        for (int jj = 0; jj < EC / 2; ++jj) {
+          const int64_t j = t.jc0 + col0 / 2 + jj;
+          if (j >= p.n) break;
+          if (p.lowerC && i < j) break;
+          const int fj = z.fb[j];
+          double re = 0.0, im = 0.0;
+          if (ei && fj) {
+            const int sc = (ei - 2048) + (fj - 2048) - 14;
+            re = value(2 * jj, sc);
+            im = value(2 * jj + 1, sc);
+          }
+          cplx v = cmul(p.alpha, mkc(re, im));
+          if (p.epi == EPI_XY) {
+            const cplx v1 = p.P[i + j * p.ldp];
+            const double s1 = p.c1[j], s2 = p.c2[j];
+            const cplx x1 = cscale(v1, 0.5 * s1), x2 = cscale(v, 0.5 * s2);
+            C[i + j * p.ldc] = cadd(x1, x2);
+            p.Y[i + j * p.ldy] = csub(x2, x1);
+          } else {
+            if (use_beta) v = cadd(v, cmul(p.beta, C[i + j * p.ldc]));
+            C[i + j * p.ldc] = v;
+          }
+        }
+      } else {
+        const bool use_beta = p.beta != 0.0;
+#pragma unroll
+        for (int jj = 0; jj < EC; ++jj) {
+          const int64_t j = t.jc0 + col0 + jj;
+          if (j >= p.n) break;
+          if (p.lowerC && i < j) break;
+          const int fj = z.fb[j];
+          double v = 0.0;
+          if (ei && fj) v = value(jj, (ei - 2048) + (fj - 2048) - 14);
+          v *= p.alpha;
+          if (use_beta) v += p.beta * C[i + j * p.ldc];
+          C[i + j * p.ldc] = v;
         }
       }
-      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -709,8 +819,8 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
   }
   if (failed && warp == 0 && lane == 0) {
     // the copies still in flight land before the CTA leaves (bounded)
-    for (int kt = issued - UM_STAGES < 0 ? 0 : issued - UM_STAGES; kt < issued; ++kt)
-      um_wait(full0 + 8 * (kt % UM_STAGES), (kt / UM_STAGES) & 1, nullptr, ab, UM_WAIT_CYCLES);
+    for (uint32_t g = issued > UM_STAGES ? issued - UM_STAGES : 0; g < issued; ++g)
+      um_wait(full0 + 8 * (g % UM_STAGES), (g / UM_STAGES) & 1, nullptr, ab, UM_WAIT_CYCLES);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -718,64 +828,7 @@ __global__ void __launch_bounds__(384, 1) oz_umma_kernel(const OzArgs<T> z, cons
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
   }
-  if (failed) {
-    if (threadIdx.x == 0 && p.status) dev_fail((int64_t*)p.status, BSE_ERR_TIMEOUT, 0);
-    return;
-  }
-  if (warp < 4) return;
-  // epilogue: thread = one row of the tile and columns [col0, col0 + 32) of
-  // its 64 real columns; complex -- real columns (2j, 2j+1) are (Re, Im) of
-  // logical column jc0 + col0/2 + j; real -- column jc0 + col0 + q
-  const int64_t i = i0 + (warp & 3) * 32 + lane;
-  if (i >= p.m) return;
-  const int col0 = ((warp - 4) >> 2) * EC;
-  const int ei = z.ea[i];
-  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  auto value = [&](int q, int sc) -> double {
-    if ((nanmask >> q) & 1u) return qnan;
-    return ldexp((double)hi[q], sc - 28) + ldexp((double)lo[q], sc - 45);
-  };
-  if constexpr (CPLX) {
-    const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
-#pragma unroll
-    for (int jj = 0; jj < EC / 2; ++jj) {
-      const int64_t j = jc0 + col0 / 2 + jj;
-      if (j >= p.n) break;
-      if (p.lowerC && i < j) break;
-      const int fj = z.fb[j];
-      double re = 0.0, im = 0.0;
-      if (ei && fj) {
-        const int sc = (ei - 2048) + (fj - 2048) - 14;
-        re = value(2 * jj, sc);
-        im = value(2 * jj + 1, sc);
-      }
-      cplx v = cmul(p.alpha, mkc(re, im));
-      if (p.epi == EPI_XY) {
-        const cplx v1 = p.P[i + j * p.ldp];
-        const double s1 = p.c1[j], s2 = p.c2[j];
-        const cplx x1 = cscale(v1, 0.5 * s1), x2 = cscale(v, 0.5 * s2);
-        p.C[i + j * p.ldc] = cadd(x1, x2);
-        p.Y[i + j * p.ldy] = csub(x2, x1);
-      } else {
-        if (use_beta) v = cadd(v, cmul(p.beta, p.C[i + j * p.ldc]));
-        p.C[i + j * p.ldc] = v;
-      }
-    }
-  } else {
-    const bool use_beta = p.beta != 0.0;
-#pragma unroll
-    for (int jj = 0; jj < EC; ++jj) {
-      const int64_t j = jc0 + col0 + jj;
-      if (j >= p.n) break;
-      if (p.lowerC && i < j) break;
-      const int fj = z.fb[j];
-      double v = 0.0;
-      if (ei && fj) v = value(jj, (ei - 2048) + (fj - 2048) - 14);
-      v *= p.alpha;
-      if (use_beta) v += p.beta * p.C[i + j * p.ldc];
-      p.C[i + j * p.ldc] = v;
-    }
-  }
+  if (failed && threadIdx.x == 0 && p.status) dev_fail((int64_t*)p.status, BSE_ERR_TIMEOUT, 0);
 }
 
 // ---- real operands -------------------------------------------------------------
@@ -864,6 +917,23 @@ size_t oz_work_bytes(int64_t maxdim, int slices) {
 }
 
 // ---- tcgen05 engine: tensor maps and launch ------------------------------------
+// SM count of the current device (looked up once per device)
+static int64_t oz_device_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> sms_of[kMaxDev];
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError(), dev = -1;
+  if (dev >= 0 && dev < kMaxDev) sms = sms_of[dev].load(std::memory_order_relaxed);
+  if (!sms) {
+    if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 152;  // GB300
+    }
+    if (dev >= 0 && dev < kMaxDev) sms_of[dev].store(sms, std::memory_order_relaxed);
+  }
+  return sms;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -908,10 +978,17 @@ static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_
     const bse_status r = set_smem_attr((const void*)oz_umma_kernel<S, T>, UmLayout<S>::SMEM);
     if (r) return r;
   }
-  dim3 grid((unsigned)((ncols_real + UM_BN - 1) / UM_BN), (unsigned)((z.Mp + UM_BM - 1) / UM_BM));
+  // persistent: one CTA per SM (its shared memory allows no second one), or
+  // one per tile when there are fewer
+  OzArgs<T> za = z;
+  za.ncols_real = ncols_real;
+  const int64_t layers = z.p.kchunk > 0 ? (z.p.k + z.p.kchunk - 1) / z.p.kchunk : 1;
+  const int64_t tiles = ((ncols_real + UM_BN - 1) / UM_BN) * ((z.Mp + UM_BM - 1) / UM_BM) * layers;
+  const int64_t sms = oz_device_sms();
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
   prof_tc_begin(s);
   prof_launch_begin(s);
-  oz_umma_kernel<S, T><<<grid, 384, UmLayout<S>::SMEM, s>>>(z, ta, tb);
+  oz_umma_kernel<S, T><<<grid, UM_THREADS, UmLayout<S>::SMEM, s>>>(za, ta, tb);
   prof_launch_end(s, "oz_umma_kernel");
   prof_tc_end(s, flops);
   bse_count_launch();
