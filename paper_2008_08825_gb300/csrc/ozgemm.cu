@@ -470,6 +470,50 @@ struct UmLayout {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// (-1)^neg (hi 2^17 + lo) 2^e as the nearest double (one rounding, ties to
+// even), with integer instructions only: the exact 128-bit value is
+// normalised and rounded on its bit pattern (FP64 instructions are the
+// slowest unit of this part).  Results outside the normal range take ldexp.
+__device__ __forceinline__ double um_to_double(int64_t hi, int32_t lo, int e, bool neg) {
+  uint64_t vl = ((uint64_t)hi << 17) | (uint64_t)(uint32_t)lo;  // 128-bit two's complement
+  uint64_t vh = (uint64_t)(hi >> 47);
+  if ((int64_t)vh < 0) {  // magnitude
+    vl = ~vl + 1;
+    vh = ~vh + (vl == 0 ? 1 : 0);
+    neg = !neg;
+  }
+  if (vh == 0 && vl == 0) return 0.0;
+  int t = vh ? 127 - __clzll((long long)vh) : 63 - __clzll((long long)vl);  // top bit
+  uint64_t mant;
+  if (t <= 52) {
+    mant = vl << (52 - t);
+  } else {
+    const int sh = t - 52;  // 1 .. 75
+    uint64_t rb, st;
+    if (sh < 64) {
+      mant = (vl >> sh) | (vh << (64 - sh));
+      rb = (vl >> (sh - 1)) & 1;
+      st = vl & ((1ull << (sh - 1)) - 1);
+    } else if (sh == 64) {
+      mant = vh;
+      rb = vl >> 63;
+      st = vl & ~(1ull << 63);
+    } else {
+      mant = vh >> (sh - 64);
+      rb = (vh >> (sh - 65)) & 1;
+      st = (vh & ((1ull << (sh - 65)) - 1)) | vl;
+    }
+    if (rb && (st || (mant & 1))) ++mant;
+    if (mant >> 53) mant >>= 1, ++t;
+  }
+  const int be = t + e + 1023;
+  if (be <= 0 || be >= 2047) {
+    const double d = ldexp((double)mant, t - 52 + e);
+    return neg ? -d : d;
+  }
+  return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1))));
+}
+
 // bounded wait on an mbarrier phase; false on timeout (which sets the abort
 // flag) or, when abort_flag is given, as soon as another role has aborted
 __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
@@ -761,12 +805,38 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
       T* C = p.C + (p.kchunk > 0 ? t.tz * p.cstride : 0);
       const int ei = z.ea[i];
       const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-      auto value = [&](int q, int sc) -> double {
+      // value of column q = (hi 2^17 + lo) 2^(sc - 45); alpha = -1 folds into
+      // the sign for free
+      auto value = [&](int q, int sc, bool neg) -> double {
         if ((nanmask >> q) & 1u) return qnan;
-        return ldexp((double)hi[q], sc - 28) + ldexp((double)lo[q], sc - 45);
+        return um_to_double(hi[q], lo[q], sc - 45, neg);
       };
       if constexpr (CPLX) {
         const bool use_beta = p.beta.x != 0.0 || p.beta.y != 0.0;
+        // alpha = +-1 and beta in {0, 1} (every product but the fused X/Y
+        // setup): no FP64 work but the one add of C
+        const bool fast = p.epi != EPI_XY && p.alpha.y == 0.0 && (p.alpha.x == 1.0 || p.alpha.x == -1.0) &&
+                          p.beta.y == 0.0 && (p.beta.x == 0.0 || p.beta.x == 1.0);
+        const bool aneg = p.alpha.x < 0.0;
+        if (fast) {
+#pragma unroll
+          for (int jj = 0; jj < EC / 2; ++jj) {
+            const int64_t j = t.jc0 + col0 / 2 + jj;
+            if (j >= p.n) break;
+            if (p.lowerC && i < j) break;
+            const int fj = z.fb[j];
+            double re = 0.0, im = 0.0;
+            if (ei && fj) {
+              const int sc = (ei - 2048) + (fj - 2048) - 14;
+              re = value(2 * jj, sc, aneg);
+              im = value(2 * jj + 1, sc, aneg);
+            }
+            cplx v = mkc(re, im);
+            if (use_beta) v = cadd(v, C[i + j * p.ldc]);
+            C[i + j * p.ldc] = v;
+          }
+          continue;
+        }
 #pragma unroll
         for (int jj = 0; jj < EC / 2; ++jj) {
           const int64_t j = t.jc0 + col0 / 2 + jj;
@@ -776,8 +846,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
           double re = 0.0, im = 0.0;
           if (ei && fj) {
             const int sc = (ei - 2048) + (fj - 2048) - 14;
-            re = value(2 * jj, sc);
-            im = value(2 * jj + 1, sc);
+            re = value(2 * jj, sc, false);
+            im = value(2 * jj + 1, sc, false);
           }
           cplx v = cmul(p.alpha, mkc(re, im));
           if (p.epi == EPI_XY) {
@@ -793,6 +863,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
         }
       } else {
         const bool use_beta = p.beta != 0.0;
+        const bool fast = (p.alpha == 1.0 || p.alpha == -1.0) && (p.beta == 0.0 || p.beta == 1.0);
 #pragma unroll
         for (int jj = 0; jj < EC; ++jj) {
           const int64_t j = t.jc0 + col0 + jj;
@@ -800,9 +871,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
           if (p.lowerC && i < j) break;
           const int fj = z.fb[j];
           double v = 0.0;
-          if (ei && fj) v = value(jj, (ei - 2048) + (fj - 2048) - 14);
-          v *= p.alpha;
-          if (use_beta) v += p.beta * C[i + j * p.ldc];
+          if (ei && fj) v = value(jj, (ei - 2048) + (fj - 2048) - 14, fast && p.alpha < 0.0);
+          if (!fast) v *= p.alpha;
+          if (use_beta) v = fast ? v + C[i + j * p.ldc] : v + p.beta * C[i + j * p.ldc];
           C[i + j * p.ldc] = v;
         }
       }
