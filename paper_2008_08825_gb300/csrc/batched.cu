@@ -20,14 +20,29 @@
 //   the k smallest singular values; twisted-factorisation vectors split into
 //   U_B, V_B; one Newton-Schulz step on each; U = Q U_B, V = P V_B one
 //   reflector at a time; X, Y from L1 U and L2 V through the fused epilogue.
-// A whole instance stays on one SM, so nothing synchronises across CTAs;
-// the only global atomic is the queue counter.
+// The Cholesky method's large instances (n >= BATCH_TEAM_MIN_N) are solved by
+// a team: the CTAs of one thread-block cluster (BATCH_TEAM CTAs on as many
+// SMs).  The team splits the heavy stages -- the Cholesky panels and
+// trailing updates, both congruence products (by output tiles), and every
+// column of the Householder tridiagonalisation (matrix-vector rows, rank-2
+// update columns; the new w is exchanged through distributed shared memory)
+// -- and meets at cluster barriers between dependent steps; the cheap k-sized
+// tail (bisection, vectors, back-transformation, X and Y) runs on the team's
+// first CTA.  Without teams a whole instance stays on one SM; the only global
+// atomics are the queue counters.
 #include <float.h>
+
+#include <atomic>
+#include <cooperative_groups.h>
 
 #include "gemm_tile.cuh"
 #include "kernels.cuh"
 
+namespace cg = cooperative_groups;
+
 constexpr int BT = 256;       // threads per CTA
+constexpr int BATCH_TEAM = 4;          // CTAs (one cluster) per large Alg. 2 instance
+constexpr int BATCH_TEAM_MIN_N = 448;  // instances this large are solved by a team
 constexpr int CNB = 32;       // Cholesky block
 constexpr int CLD = CNB + 1;
 
@@ -106,9 +121,45 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
 
 __device__ __forceinline__ double cta_min(double v, double* red) { return -cta_max(-v, red); }
 
+// The CTAs that solve one instance together: a cluster (size > 1) or the
+// calling CTA alone (size 1).
+struct Team {
+  int rank, size;
+};
+
+// Barrier of the team; for a cluster, global-memory writes before it are
+// visible to every CTA of the team after it (device-scope fences on both
+// sides of the cluster barrier, so no CTA keeps stale lines in its L1).
+__device__ __forceinline__ void team_sync(const Team& tm) {
+  if (tm.size > 1) {
+    __threadfence();
+    cg::this_cluster().sync();
+    __threadfence();
+  } else {
+    __syncthreads();
+  }
+}
+
+// The tiles t = rank, rank + size, ... of one product (the order of gemm_cta).
+template <typename T, int BK>
+__device__ __forceinline__ void gemm_team(const GemmParams<T>& p, const Team& tm) {
+  if (p.m <= 0 || p.n <= 0) return;
+  int64_t t = 0;
+  for (int64_t i0 = 0; i0 < p.m; i0 += GBM)
+    for (int64_t j0 = 0; j0 < p.n; j0 += GBN) {
+      if (p.lowerC && j0 > i0 + GBM - 1) continue;
+      if (t++ % tm.size != tm.rank) continue;
+      gemm_tile<T, BK>(p, i0, j0);
+    }
+}
+
 // ---- Cholesky of the lower triangle of L (n x n, ld n), block CNB ----------
+// Every CTA of a team factors the diagonal block in its own shared memory
+// (the same arithmetic, so the same bits and the same pivot decision); the
+// team's first CTA writes it, and the panel and trailing update are split by
+// output tiles.
 __device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx* S, cplx* Iv, int* flag,
-                          int64_t err_code) {
+                          int64_t err_code, Team tm = Team{0, 1}) {
   const int tid = threadIdx.x;
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), mone = mkc(-1.0, 0.0);
   for (int64_t k0 = 0; k0 < n; k0 += CNB) {
@@ -125,8 +176,10 @@ __device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx*
         const double dd = S[j + j * CLD].x;
         if (!(dd > 0.0)) {
           *flag = 1;
-          status[0] = err_code;
-          status[1] = k0 + j + 1;
+          if (tm.rank == 0) {
+            status[0] = err_code;
+            status[1] = k0 + j + 1;
+          }
         } else {
           S[j + j * CLD] = mkc(sqrt(dd), 0.0);
         }
@@ -159,33 +212,41 @@ __device__ bool cta_potrf(int64_t n, cplx* L, cplx* Linv, int64_t* status, cplx*
       }
     }
     __syncthreads();
-    for (int e = tid; e < bs * bs; e += BT) {
-      const int i = e % bs, j = e / bs;
-      L[IDX2(k0 + i, k0 + j, n)] = (i >= j) ? S[i + j * CLD] : zero;
-      Linv[i + j * CNB] = (i >= j) ? Iv[i + j * CLD] : zero;
-    }
+    if (tm.rank == 0)
+      for (int e = tid; e < bs * bs; e += BT) {
+        const int i = e % bs, j = e / bs;
+        L[IDX2(k0 + i, k0 + j, n)] = (i >= j) ? S[i + j * CLD] : zero;
+        Linv[i + j * CNB] = (i >= j) ? Iv[i + j * CLD] : zero;
+      }
     __threadfence_block();
-    __syncthreads();
+    team_sync(tm);
     const int64_t m2 = n - k0 - bs;
     if (m2 <= 0) continue;
     cplx* A21 = L + IDX2(k0 + bs, k0, n);
     cplx* A22 = L + IDX2(k0 + bs, k0 + bs, n);
     GemmParams<cplx> p = gemm_params<cplx>(m2, bs, bs, OPN, A21, n, OPC, Linv, CNB, one, zero, A21, n);
     p.triB = TRI_UP;
-    gemm_cta<cplx, 8>(p);
+    gemm_team<cplx, 8>(p, tm);
     __threadfence_block();
+    if (tm.size > 1) team_sync(tm);
     GemmParams<cplx> q = gemm_params<cplx>(m2, m2, bs, OPN, A21, n, OPC, A21, n, mone, one, A22, n);
     q.lowerC = 1;
-    gemm_cta<cplx, 8>(q);
+    gemm_team<cplx, 8>(q, tm);
     __threadfence_block();
-    __syncthreads();
+    team_sync(tm);
   }
   return true;
 }
 
 // ---- unblocked Householder tridiagonalisation of the lower triangle of M ----
 // Reflector j is stored explicitly in M(j+1:, j) (unit first entry).
-__device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, cplx* vs, cplx* ws, double* red) {
+// In a team every CTA forms the reflector and v in its own shared memory (the
+// same arithmetic on the same column); w = tau A22 v is split by rows, each
+// CTA storing its rows of w into every team member's `ws` (distributed
+// shared memory), and the rank-2 update by columns.  The first CTA writes v,
+// tau, d and e, after the team has read column j.
+__device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, cplx* vs, cplx* ws, double* red,
+                          Team tm = Team{0, 1}) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ cplx h_tau, h_scal, h_alpha;
   __shared__ double h_beta;
@@ -196,7 +257,6 @@ __device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, c
     nrm = cta_sum(nrm, red);
     if (tid == 0) {
       const cplx alpha = M[IDX2(base, j, n)];
-      d[j] = M[IDX2(j, j, n)].x;
       if (nrm == 0.0 && alpha.y == 0.0) {
         h_tau = mkc(0.0, 0.0);
         h_beta = alpha.x;
@@ -208,18 +268,20 @@ __device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, c
         h_tau = mkc((beta - alpha.x) / beta, -alpha.y / beta);
         h_scal = cdiv(mkc(1.0, 0.0), mkc(alpha.x - beta, alpha.y));
       }
-      tau[j] = h_tau;
-      e[j] = h_beta;
+      if (tm.rank == 0) {
+        d[j] = M[IDX2(j, j, n)].x;
+        tau[j] = h_tau;
+        e[j] = h_beta;
+      }
     }
     __syncthreads();
-    for (int64_t r = tid; r < m; r += BT) {
-      const cplx v = (r == 0) ? mkc(1.0, 0.0) : cmul(M[IDX2(base + r, j, n)], h_scal);
-      vs[r] = v;
-      M[IDX2(base + r, j, n)] = v;
-    }
+    for (int64_t r = tid; r < m; r += BT) vs[r] = (r == 0) ? mkc(1.0, 0.0) : cmul(M[IDX2(base + r, j, n)], h_scal);
     __syncthreads();
-    // w = A22 v: lower part (c <= r) by rows, strict upper by columns
-    for (int64_t r = tid; r < m; r += BT) {
+    // w = tau A22 v for this CTA's rows: lower part (c <= r) by rows, strict
+    // upper by columns
+    const int64_t per = (m + tm.size - 1) / tm.size, rb0 = tm.rank * per;
+    const int64_t rb1 = rb0 + per < m ? rb0 + per : m;
+    for (int64_t r = rb0 + tid; r < rb1; r += BT) {
       cplx acc0 = mkc(0.0, 0.0), acc1 = mkc(0.0, 0.0);
       const cplx* Ar = M + IDX2(base + r, base, n);
       int64_t c = 0;
@@ -230,9 +292,16 @@ __device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, c
       if (c <= r) cfma(acc0, Ar[c * n], vs[c]);
       const cplx* Ac = M + IDX2(base, base + r, n);
       for (int64_t rr = r + 1; rr < m; ++rr) cfma_cj(acc1, Ac[rr], vs[rr]);
-      ws[r] = cmul(h_tau, cadd(acc0, acc1));
+      const cplx wr = cmul(h_tau, cadd(acc0, acc1));
+      if (tm.size > 1) {
+        for (int q = 0; q < tm.size; ++q) cg::this_cluster().map_shared_rank(ws, q)[r] = wr;
+      } else {
+        ws[r] = wr;
+      }
     }
-    __syncthreads();
+    team_sync(tm);
+    if (tm.rank == 0)
+      for (int64_t r = tid; r < m; r += BT) M[IDX2(base + r, j, n)] = vs[r];
     double dre = 0.0, dim = 0.0;
     for (int64_t r = tid; r < m; r += BT) {
       const cplx t = cmul(cconj(ws[r]), vs[r]);
@@ -244,8 +313,9 @@ __device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, c
     __syncthreads();
     for (int64_t r = tid; r < m; r += BT) ws[r] = cadd(ws[r], cmul(h_alpha, vs[r]));
     __syncthreads();
-    // A22 -= v w^H + w v^H (lower): warp per column, lanes over rows
-    for (int64_t c = warp; c < m; c += BT / 32) {
+    // A22 -= v w^H + w v^H (lower): warp per column, lanes over rows; the
+    // team's CTAs take every size-th column
+    for (int64_t c = tm.rank + (int64_t)tm.size * warp; c < m; c += (int64_t)tm.size * (BT / 32)) {
       const cplx wc = cconj(ws[c]), vc = cconj(vs[c]);
       cplx* Acol = M + IDX2(base, base + c, n);
       for (int64_t r = c + lane; r < m; r += 32) {
@@ -255,9 +325,9 @@ __device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, c
         Acol[r] = a;
       }
     }
-    __syncthreads();
+    team_sync(tm);
   }
-  if (tid == 0) d[n - 1] = M[IDX2(n - 1, n - 1, n)].x;
+  if (tid == 0 && tm.rank == 0) d[n - 1] = M[IDX2(n - 1, n - 1, n)].x;
   __syncthreads();
 }
 
@@ -274,7 +344,10 @@ __device__ __forceinline__ int bsturm(const double* a, const double* e2, int64_t
 }
 
 // ---- the whole instance -----------------------------------------------------
-__device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* red, cplx* S, cplx* Iv, int* flag) {
+// A team solves the instance together up to the tridiagonal matrix (every
+// CTA returns from here at the same point); the rest runs on its first CTA.
+__device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* red, cplx* S, cplx* Iv, int* flag,
+                               Team tm = Team{0, 1}) {
   const int64_t n = D.n, k = D.k;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   InstWs w;
@@ -282,7 +355,7 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
   int64_t* st = D.status;
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
   // form M1 (full) and M2 (lower, into L)
-  for (int64_t q = tid; q < n * n; q += BT) {
+  for (int64_t q = tm.rank * BT + tid; q < n * n; q += (int64_t)tm.size * BT) {
     const int64_t i = q % n, j = q / n;
     if (i >= j) {
       const cplx a = D.A[IDX2(i, j, n)], b = D.B[IDX2(i, j, n)];
@@ -294,21 +367,22 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
     }
   }
   __threadfence_block();
-  __syncthreads();
-  if (!cta_potrf(n, w.L, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_AMINUSB)) return;
+  team_sync(tm);
+  if (!cta_potrf(n, w.L, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_AMINUSB, tm)) return;
   // W = M1 L ; M = L^H W (lower) into M1
   GemmParams<cplx> p1 = gemm_params<cplx>(n, n, n, OPN, w.M1, n, OPN, w.L, n, one, zero, w.W, n);
   p1.triB = TRI_LO;
-  gemm_cta<cplx, 8>(p1);
+  gemm_team<cplx, 8>(p1, tm);
   __threadfence_block();
-  __syncthreads();
+  team_sync(tm);
   GemmParams<cplx> p2 = gemm_params<cplx>(n, n, n, OPC, w.L, n, OPN, w.W, n, one, zero, w.M1, n);
   p2.triA = TRI_UP;
   p2.lowerC = 1;
-  gemm_cta<cplx, 8>(p2);
+  gemm_team<cplx, 8>(p2, tm);
   __threadfence_block();
-  __syncthreads();
-  cta_hetrd(n, w.M1, w.tau, w.d, w.e, vs, wsv, red);
+  team_sync(tm);
+  cta_hetrd(n, w.M1, w.tau, w.d, w.e, vs, wsv, red, tm);
+  if (tm.rank != 0) return;
   // tridiagonal: bounds, bisection for the k smallest
   double tn = 0.0, em = 0.0, lo = 1e308, hi = -1e308;
   for (int64_t i = tid; i < n; i += BT) {
@@ -810,18 +884,110 @@ __global__ void __launch_bounds__(BT, 1) batched_chol_kernel(const BatchDesc* __
   }
 }
 
+// Alg. 2 with teams: the clusters (BATCH_TEAM CTAs each) take the first
+// `nbig` instances of the size-ordered queue one at a time, a team per
+// instance; when none is left, every CTA takes the remaining (small)
+// instances alone from a second counter.
+__global__ void __launch_bounds__(BT, 1) batched_chol_team_kernel(const BatchDesc* __restrict__ desc, int64_t count,
+                                                                  int64_t nbig, int* counters) {
+  extern __shared__ cplx dyn[];
+  cplx* vs = dyn;                    // 1024
+  cplx* wsv = dyn + 1024;            // 1024
+  cplx* S = dyn + 2048;              // CNB x CLD
+  cplx* Iv = S + CNB * CLD;          // CNB x CLD
+  __shared__ double red[BT / 32];
+  __shared__ int next, flag;
+  cg::cluster_group cl = cg::this_cluster();
+  const Team tm{(int)cl.block_rank(), (int)cl.num_blocks()};
+  for (;;) {
+    if (tm.rank == 0 && threadIdx.x == 0) {
+      const int i = atomicAdd(counters, 1);
+      for (int q = 0; q < tm.size; ++q) *cl.map_shared_rank(&next, q) = i;
+    }
+    cl.sync();
+    const int idx = next;
+    cl.sync();
+    if (idx >= nbig) break;
+    solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag, tm);
+    __syncthreads();
+  }
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)nbig + atomicAdd(counters + 1, 1);
+    __syncthreads();
+    const int idx = next;
+    __syncthreads();
+    if (idx >= count) break;
+    solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag);
+    __syncthreads();
+  }
+}
+
 size_t batched_smem_bytes() { return sizeof(cplx) * (2048 + 2 * CNB * CLD); }
 
-bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid, int method) {
+int batched_team_min_n() { return BATCH_TEAM_MIN_N; }
+
+// Largest grid of whole teams that can be resident at once (0: none), looked
+// up once per device.
+static int team_grid_query(size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = BATCH_TEAM, attr[0].val.clusterDim.y = 1, attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(BATCH_TEAM, 1, 1);
+  cfg.blockDim = dim3(BT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, (void*)batched_chol_team_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return clusters * BATCH_TEAM;
+}
+
+static int team_grid(size_t smem) {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> grid_of[kMaxDev];  // grid + 1 (0: not yet looked up)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return team_grid_query(smem);
+  }
+  int g = grid_of[dev].load(std::memory_order_relaxed);
+  if (!g) {
+    g = team_grid_query(smem) + 1;
+    grid_of[dev].store(g, std::memory_order_relaxed);
+  }
+  return g - 1;
+}
+
+bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid, int method,
+                               int64_t nbig) {
   const size_t smem = batched_smem_bytes();
   bse_status r = set_smem_attr((const void*)batched_chol_kernel, (int)smem);
   if (!r) r = set_smem_attr((const void*)batched_svd_kernel, (int)smem);
+  if (!r) r = set_smem_attr((const void*)batched_chol_team_kernel, (int)smem);
   if (r) return r;
-  BSE_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
-  if (method == BSE_METHOD_SVD)
+  BSE_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
+  const int tgrid = (method == BSE_METHOD_CHOL && nbig > 0) ? team_grid(smem) : 0;
+  if (tgrid > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = BATCH_TEAM, attr[0].val.clusterDim.y = 1, attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)tgrid, 1, 1);
+    cfg.blockDim = dim3(BT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BSE_CUDA(cudaLaunchKernelEx(&cfg, batched_chol_team_kernel, (const BatchDesc*)desc, count, nbig, counter));
+  } else if (method == BSE_METHOD_SVD) {
     batched_svd_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
-  else
+  } else {
     batched_chol_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
+  }
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   return BSE_OK;

@@ -749,7 +749,9 @@ static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* 
   BSE_CUDA(cudaMemcpyAsync(ddesc, h->bdesc_host, batched_desc_bytes() * count, cudaMemcpyHostToDevice, s));
   BSE_CUDA(cudaMemsetAsync(dstat, 0, 16 * count, s));
   const int grid = (int)std::min<int64_t>(count, (int64_t)h->sms * h->batch_cps);
-  TRY(batched_chol_launch(s, ddesc, count, counter, grid, method));
+  int64_t nbig = 0;  // the table is sorted by decreasing n
+  while (nbig < count && n[order[nbig]] >= batched_team_min_n()) ++nbig;
+  TRY(batched_chol_launch(s, ddesc, count, counter, grid, method, nbig));
   if (dstatus_out) *dstatus_out = dstat;
   return BSE_OK;
 }

@@ -131,8 +131,11 @@ size_t batched_svd_inst_bytes(int64_t n, int64_t k);
 cudaError_t single_chol_prepare();
 cudaError_t single_chol_launch(cudaStream_t s, int64_t n, int64_t k, const void* A, const void* B, double* omega,
                                void* X, void* Y, char* ws, int64_t* status);
+// counter: two ints (queue counters); nbig: the first nbig instances of the
+// size-ordered table are large enough for a team of CTAs (Alg. 2 only)
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid,
-                               int method);
+                               int method, int64_t nbig);
+int batched_team_min_n();
 
 // ---- ozgemm.cu ----  FP64-accurate complex GEMM on the BF16 tensor cores
 enum { OZ_ENGINE_TCGEN05 = 0, OZ_ENGINE_MMA_SYNC = 1 };
