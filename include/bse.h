@@ -110,7 +110,15 @@ typedef enum {
    * records BSE_ERR_TIMEOUT; the solve then returns BSE_ERR_TIMEOUT and
    * writes no output.  A tiny value forces that path (a test uses it); the
    * handle stays usable. */
-  BSE_OPT_TC_WAIT_CYCLES = 4
+  BSE_OPT_TC_WAIT_CYCLES = 4,
+  /* Batched Alg. 2: instances with n >= BSE_OPT_BATCH_TEAM_MIN_N (default
+   * 448) are solved by a team of BSE_OPT_BATCH_TEAM CTAs (1, 2, 4 or 8;
+   * default 4), one thread-block cluster on as many SMs, so the largest
+   * instances do not set the batch's critical path; 1 puts every instance
+   * on one CTA.  Neither changes a result bit (the team splits work, not
+   * sums).  Chosen per workload by the autotuner (autotune.py). */
+  BSE_OPT_BATCH_TEAM = 5,
+  BSE_OPT_BATCH_TEAM_MIN_N = 6
 } bse_option;
 bse_status bse_set_option(bse_handle h, int option, int64_t value);
 

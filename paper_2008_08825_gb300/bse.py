@@ -157,6 +157,12 @@ class Handle:
         cycles (0 restores the default, about 1 s)."""
         _check(lib().bse_set_option(self._h, 4, int(value)))
 
+    def set_batch_team(self, team: int, min_n: int | None = None) -> None:
+        """Batched Alg. 2: CTAs per team (1, 2, 4, 8) for instances with n >= min_n."""
+        _check(lib().bse_set_option(self._h, 5, int(team)))
+        if min_n is not None:
+            _check(lib().bse_set_option(self._h, 6, int(min_n)))
+
     def set_batch_ctas_per_sm(self, value: int) -> None:
         """Batched solves: 1 or 2 resident CTAs per SM for the persistent kernel."""
         _check(lib().bse_set_option(self._h, 2, int(value)))

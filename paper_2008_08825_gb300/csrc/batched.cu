@@ -41,8 +41,8 @@
 namespace cg = cooperative_groups;
 
 constexpr int BT = 256;       // threads per CTA
-constexpr int BATCH_TEAM = 4;          // CTAs (one cluster) per large Alg. 2 instance
-constexpr int BATCH_TEAM_MIN_N = 448;  // instances this large are solved by a team
+constexpr int BATCH_TEAM = 4;          // default CTAs (one cluster) per large Alg. 2 instance
+constexpr int BATCH_TEAM_MIN_N = 448;  // default: instances this large are solved by a team
 constexpr int CNB = 32;       // Cholesky block
 constexpr int CLD = CNB + 1;
 
@@ -127,14 +127,13 @@ struct Team {
   int rank, size;
 };
 
-// Barrier of the team; for a cluster, global-memory writes before it are
-// visible to every CTA of the team after it (device-scope fences on both
-// sides of the cluster barrier, so no CTA keeps stale lines in its L1).
+// Barrier of the team.  For a cluster it is barrier.cluster.arrive (release)
+// + barrier.cluster.wait (acquire), both at cluster scope, so the global and
+// distributed-shared-memory writes of every team member before it are
+// visible to every member after it.
 __device__ __forceinline__ void team_sync(const Team& tm) {
   if (tm.size > 1) {
-    __threadfence();
     cg::this_cluster().sync();
-    __threadfence();
   } else {
     __syncthreads();
   }
@@ -328,7 +327,7 @@ __device__ void cta_hetrd(int64_t n, cplx* M, cplx* tau, double* d, double* e, c
     team_sync(tm);
   }
   if (tid == 0 && tm.rank == 0) d[n - 1] = M[IDX2(n - 1, n - 1, n)].x;
-  __syncthreads();
+  team_sync(tm);
 }
 
 __device__ __forceinline__ int bsturm(const double* a, const double* e2, int64_t n, double x, double pivmin) {
@@ -382,7 +381,8 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
   __threadfence_block();
   team_sync(tm);
   cta_hetrd(n, w.M1, w.tau, w.d, w.e, vs, wsv, red, tm);
-  if (tm.rank != 0) return;
+  // the rest is split over the team by eigenpairs: pair t belongs to CTA
+  // t % size (every member computes the same bounds)
   // tridiagonal: bounds, bisection for the k smallest
   double tn = 0.0, em = 0.0, lo = 1e308, hi = -1e308;
   for (int64_t i = tid; i < n; i += BT) {
@@ -391,8 +391,8 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
     lo = fmin(lo, w.d[i] - ol - orr);
     hi = fmax(hi, w.d[i] + ol + orr);
     if (i < n - 1) {
-      w.e2[i] = w.e[i] * w.e[i];
-      em = fmax(em, w.e2[i]);
+      if (tm.rank == 0) w.e2[i] = w.e[i] * w.e[i];
+      em = fmax(em, w.e[i] * w.e[i]);
     }
   }
   tn = cta_max(tn, red);
@@ -400,11 +400,11 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
   lo = cta_min(lo, red);
   hi = cta_max(hi, red);
   __threadfence_block();
-  __syncthreads();
+  team_sync(tm);
   const double pivmin = DBL_MIN * fmax(1.0, em), g = DBL_EPSILON * fmax(tn, DBL_MIN);
   lo -= 2.0 * DBL_EPSILON * tn + 4.0 * pivmin;
   hi += 2.0 * DBL_EPSILON * tn + 4.0 * pivmin;
-  for (int64_t t = tid; t < k; t += BT) {
+  for (int64_t t = tm.rank + (int64_t)tm.size * tid; t < k; t += (int64_t)tm.size * BT) {
     double a = lo, b = hi;
     for (int it = 0; it < 256; ++it) {
       const double mid = 0.5 * (a + b), wd = b - a;
@@ -462,10 +462,10 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
     w.c2[t] = 1.0 / sqrt(om);
   }
   __threadfence_block();
-  __syncthreads();
-  if (st[0]) return;
+  team_sync(tm);
+  if (st[0]) return;  // the same word for every member
   // Newton-Schulz: E = Z^T Z - I, Z <- Z - Z E / 2 (k x k small, plain loops)
-  for (int64_t q = tid; q < k * k; q += BT) {
+  for (int64_t q = tm.rank * BT + tid; q < k * k; q += (int64_t)tm.size * BT) {
     const int64_t a = q % k, b = q / k;
     if (a < b) continue;
     const double* za = w.Z + a * n;
@@ -477,20 +477,25 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
     w.E[b + a * k] = s;
   }
   __threadfence_block();
-  __syncthreads();
-  for (int64_t q = tid; q < n * k; q += BT) {
-    const int64_t i = q % n, c = q / n;
+  team_sync(tm);
+  // from here on a member works on its own columns c = rank, rank + size, ...
+  const int64_t kc = (k - tm.rank + tm.size - 1) / tm.size;  // this member's column count
+  for (int64_t q = tid; q < n * kc; q += BT) {
+    const int64_t i = q % n, c = tm.rank + (q / n) * tm.size;
     double s = 0.0;
     for (int64_t b = 0; b < k; ++b) s = fma(w.Z[i + b * n], w.E[b + c * k], s);
-    w.sc[q] = w.Z[q] - 0.5 * s;
+    w.sc[i + c * n] = w.Z[i + c * n] - 0.5 * s;
   }
   __threadfence_block();
   __syncthreads();
-  for (int64_t q = tid; q < n * k; q += BT) w.VM[q] = mkc(w.sc[q], 0.0);
+  for (int64_t q = tid; q < n * kc; q += BT) {
+    const int64_t i = q % n, c = tm.rank + (q / n) * tm.size;
+    w.VM[i + c * n] = mkc(w.sc[i + c * n], 0.0);
+  }
   __threadfence_block();
   __syncthreads();
   // V_M = H_0 ... H_{n-2} Z, one reflector at a time; a warp owns columns
-  for (int64_t c = warp; c < k; c += BT / 32) {
+  for (int64_t c = tm.rank + (int64_t)tm.size * warp; c < k; c += (int64_t)tm.size * (BT / 32)) {
     cplx* vc = w.VM + c * n;
     for (int64_t j = n - 2; j >= 0; --j) {
       const cplx* v = w.M1 + IDX2(j + 1, j, n);
@@ -509,7 +514,7 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
   __threadfence_block();
   __syncthreads();
   // P = L^{-H} V_M, column by column (a warp owns a column)
-  for (int64_t c = warp; c < k; c += BT / 32) {
+  for (int64_t c = tm.rank + (int64_t)tm.size * warp; c < k; c += (int64_t)tm.size * (BT / 32)) {
     const cplx* vmc = w.VM + c * n;
     cplx* pc = w.P + c * n;
     for (int64_t i = n - 1; i >= 0; --i) {
@@ -525,13 +530,13 @@ __device__ void solve_instance(const BatchDesc& D, cplx* vs, cplx* wsv, double* 
     }
   }
   __threadfence_block();
-  __syncthreads();
+  team_sync(tm);
   // X, Y: v2 = L V_M, X = (c1 P + c2 v2)/2, Y = (c2 v2 - c1 P)/2
   GemmParams<cplx> p3 = gemm_params<cplx>(n, k, n, OPN, w.L, n, OPN, w.VM, n, one, zero, D.X, n);
   p3.triA = TRI_LO;
   p3.epi = EPI_XY;
   p3.P = w.P, p3.ldp = n, p3.c1 = w.c1, p3.c2 = w.c2, p3.Y = D.Y, p3.ldy = n;
-  gemm_cta<cplx, 8>(p3);
+  gemm_team<cplx, 8>(p3, tm);
 }
 
 // ---- Alg. 3 for one instance --------------------------------------------------
@@ -924,16 +929,17 @@ __global__ void __launch_bounds__(BT, 1) batched_chol_team_kernel(const BatchDes
 
 size_t batched_smem_bytes() { return sizeof(cplx) * (2048 + 2 * CNB * CLD); }
 
-int batched_team_min_n() { return BATCH_TEAM_MIN_N; }
+int batched_team_default() { return BATCH_TEAM; }
+int batched_team_min_n_default() { return BATCH_TEAM_MIN_N; }
 
-// Largest grid of whole teams that can be resident at once (0: none), looked
-// up once per device.
-static int team_grid_query(size_t smem) {
+// Largest grid of whole teams of `team` CTAs that can be resident at once
+// (0: none), looked up once per device and team size.
+static int team_grid_query(size_t smem, int team) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = BATCH_TEAM, attr[0].val.clusterDim.y = 1, attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(BATCH_TEAM, 1, 1);
+  attr[0].val.clusterDim.x = team, attr[0].val.clusterDim.y = 1, attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(team, 1, 1);
   cfg.blockDim = dim3(BT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.attrs = attr;
@@ -943,39 +949,40 @@ static int team_grid_query(size_t smem) {
     cudaGetLastError();
     return 0;
   }
-  return clusters * BATCH_TEAM;
+  return clusters * team;
 }
 
-static int team_grid(size_t smem) {
+static int team_grid(size_t smem, int team) {
   constexpr int kMaxDev = 64;
-  static std::atomic<int> grid_of[kMaxDev];  // grid + 1 (0: not yet looked up)
+  static std::atomic<int> grid_of[kMaxDev][4];  // grid + 1 per team size 1, 2, 4, 8 (0: not yet looked up)
+  const int slot = team == 8 ? 3 : team == 4 ? 2 : team == 2 ? 1 : 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
-    return team_grid_query(smem);
+    return team_grid_query(smem, team);
   }
-  int g = grid_of[dev].load(std::memory_order_relaxed);
+  int g = grid_of[dev][slot].load(std::memory_order_relaxed);
   if (!g) {
-    g = team_grid_query(smem) + 1;
-    grid_of[dev].store(g, std::memory_order_relaxed);
+    g = team_grid_query(smem, team) + 1;
+    grid_of[dev][slot].store(g, std::memory_order_relaxed);
   }
   return g - 1;
 }
 
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid, int method,
-                               int64_t nbig) {
+                               int64_t nbig, int team) {
   const size_t smem = batched_smem_bytes();
   bse_status r = set_smem_attr((const void*)batched_chol_kernel, (int)smem);
   if (!r) r = set_smem_attr((const void*)batched_svd_kernel, (int)smem);
   if (!r) r = set_smem_attr((const void*)batched_chol_team_kernel, (int)smem);
   if (r) return r;
   BSE_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
-  const int tgrid = (method == BSE_METHOD_CHOL && nbig > 0) ? team_grid(smem) : 0;
+  const int tgrid = (method == BSE_METHOD_CHOL && nbig > 0 && team > 1) ? team_grid(smem, team) : 0;
   if (tgrid > 0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = BATCH_TEAM, attr[0].val.clusterDim.y = 1, attr[0].val.clusterDim.z = 1;
+    attr[0].val.clusterDim.x = team, attr[0].val.clusterDim.y = 1, attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3((unsigned)tgrid, 1, 1);
     cfg.blockDim = dim3(BT, 1, 1);
     cfg.dynamicSmemBytes = smem;

@@ -53,6 +53,8 @@ struct bse_context {
   int oz_engine = OZ_ENGINE_TCGEN05;
   int64_t oz_wait = 0;  // 0: the engine's default wait limit
   int batch_cps = 1;
+  int batch_team = 0;          // 0: the library default
+  int64_t batch_team_min = 0;  // 0: the library default
 };
 
 // Makes the handle's profiler current for this thread for one entry point;
@@ -749,9 +751,11 @@ static bse_status batched_enqueue(bse_context* h, int64_t count, const int64_t* 
   BSE_CUDA(cudaMemcpyAsync(ddesc, h->bdesc_host, batched_desc_bytes() * count, cudaMemcpyHostToDevice, s));
   BSE_CUDA(cudaMemsetAsync(dstat, 0, 16 * count, s));
   const int grid = (int)std::min<int64_t>(count, (int64_t)h->sms * h->batch_cps);
+  const int team = h->batch_team ? h->batch_team : batched_team_default();
+  const int64_t team_min = h->batch_team_min ? h->batch_team_min : batched_team_min_n_default();
   int64_t nbig = 0;  // the table is sorted by decreasing n
-  while (nbig < count && n[order[nbig]] >= batched_team_min_n()) ++nbig;
-  TRY(batched_chol_launch(s, ddesc, count, counter, grid, method, nbig));
+  while (nbig < count && n[order[nbig]] >= team_min) ++nbig;
+  TRY(batched_chol_launch(s, ddesc, count, counter, grid, method, nbig, team));
   if (dstatus_out) *dstatus_out = dstat;
   return BSE_OK;
 }
@@ -956,6 +960,17 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value) {
     if (value < 0 || value > ((int64_t)1 << 36))
       return bse_internal_set_error("BSE_OPT_TC_WAIT_CYCLES must be in [0, 2^36]"), BSE_ERR_ARG;
     h->oz_wait = value;
+    return BSE_OK;
+  }
+  if (option == BSE_OPT_BATCH_TEAM) {
+    if (value != 1 && value != 2 && value != 4 && value != 8)
+      return bse_internal_set_error("BSE_OPT_BATCH_TEAM must be 1, 2, 4 or 8"), BSE_ERR_ARG;
+    h->batch_team = (int)value;
+    return BSE_OK;
+  }
+  if (option == BSE_OPT_BATCH_TEAM_MIN_N) {
+    if (value < 1) return bse_internal_set_error("BSE_OPT_BATCH_TEAM_MIN_N must be >= 1"), BSE_ERR_ARG;
+    h->batch_team_min = value;
     return BSE_OK;
   }
   if (option == BSE_OPT_BATCH_CTAS_PER_SM) {

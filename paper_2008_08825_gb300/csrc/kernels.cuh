@@ -132,10 +132,12 @@ cudaError_t single_chol_prepare();
 cudaError_t single_chol_launch(cudaStream_t s, int64_t n, int64_t k, const void* A, const void* B, double* omega,
                                void* X, void* Y, char* ws, int64_t* status);
 // counter: two ints (queue counters); nbig: the first nbig instances of the
-// size-ordered table are large enough for a team of CTAs (Alg. 2 only)
+// size-ordered table are solved by teams of `team` CTAs (Alg. 2 only; team 1
+// or nbig 0: every instance on one CTA)
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid,
-                               int method, int64_t nbig);
-int batched_team_min_n();
+                               int method, int64_t nbig, int team);
+int batched_team_default();
+int batched_team_min_n_default();
 
 // ---- ozgemm.cu ----  FP64-accurate complex GEMM on the BF16 tensor cores
 enum { OZ_ENGINE_TCGEN05 = 0, OZ_ENGINE_MMA_SYNC = 1 };
