@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--kernel-profile", action="store_true",
                     help="instead of timing steps: one warm solve per method and precision with per-kernel "
                          "event profiling (library profiling level 2), one JSON line each")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched block")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the n = 8192 accuracy block (oracle values)")
     ap.add_argument("--workload", default="n8192", choices=["n8192", "batched"],
                     help="n8192: the headline solve; batched: 512 uneven instances, lowest 32 pairs")
     return ap.parse_args()
@@ -298,6 +300,110 @@ def run_batched(args, rank, world, local):
         dist.destroy_process_group()
 
 
+BATCH_MODEL_PER_N3 = 44.0 / 3.0  # Cholesky 4/3 + congruence 16/3 + tridiagonalisation 16/3 + ... (x n^3 real flops)
+
+
+def batched_inline(dev, h, steps: int, warmup: int, methods=("chol", "svd")):
+    """The 512-instance batched workload (n log-uniform in [32, 1024], lowest
+    32 pairs each) timed inside the default run: one persistent launch per
+    step, inputs resident; value = instances per second.  The roofline
+    fraction uses the 14 2/3 n^3 per-instance model (Cholesky, congruence,
+    tridiagonalisation, k back-transformed vectors) against the FP64 peak."""
+    import numpy as np
+    import torch
+
+    from paper_2008_08825_gb300 import bse, inputs
+
+    sizes = inputs.batched_sizes()
+    inst = []
+    for i in range(len(sizes)):
+        A, B = inputs.base(int(sizes[i]), seed=i)
+        inst.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
+    flops = BATCH_MODEL_PER_N3 * float(np.sum(sizes.astype(np.float64) ** 3))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for m in methods:
+        bt = bse.Batch(inst, k=32, method=m)
+        for _ in range(max(warmup, 1)):
+            bt.run(handle=h)
+        torch.cuda.synchronize()
+        l0 = h.launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            bt.run(handle=h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        tf = flops / t / 1e12
+        out[m] = {"value": len(sizes) / t, "unit": "solves/s", "ms_per_step": t * 1e3, "steps": steps,
+                  "model_tflops": tf, "frac_of_fp64_peak": tf / (fp64_peak() / 1e3),
+                  "gpu_launches": (h.launches() - l0) // steps,
+                  "failed_instances": sum(1 for v in bt.status if v != 0)}
+    out["config"] = {"workload": "512 BSE instances, n = round(exp(U[ln 32, ln 1024])) (seed 10000), base generator "
+                                 "(instance i: seed i), lowest 32 eigenpairs, one persistent launch, FP64",
+                     "model_flops": flops, "model": "14 2/3 n^3 real flops per instance",
+                     "teams": "Alg. 2 instances with n >= 448 on a team of 4 CTAs (one cluster)"}
+    return out
+
+
+def accuracy_full_size(At, Bt, h, dev, seed_ok: bool):
+    """Accuracy at the bench's n (8192) against the stored oracle omega (tests/golden,
+    written by tests/golden/make_c3_oracle.py): the base workload and the
+    kappa(A - B) sweep 1e2 / 1e6 / 1e10, both methods, the FP64 form (its omega
+    do not depend on the vectors) and the mixed form with vectors (refined
+    omega).  Reports Table 1's quantity, the relative error of the smallest
+    omega, with the normwise and largest per-eigenvalue relative errors."""
+    import hashlib
+
+    import numpy as np
+    import torch
+
+    from paper_2008_08825_gb300 import bse, inputs
+
+    n = int(At.shape[0])
+    gold = os.path.join(ROOT, "tests", "golden")
+    out = {}
+    for case in ("base", "1e2", "1e6", "1e10"):
+        path = os.path.join(gold, f"c3_n{n}_seed0_{case}.npz")
+        if not os.path.exists(path):
+            out[case] = {"missing": os.path.basename(path)}
+            continue
+        z = np.load(path)
+        if case == "base" and seed_ok:
+            A, B = At, Bt
+            Ah, Bh = None, None
+        else:
+            if case == "base":
+                Ah, Bh = inputs.base(n, 0)
+            else:
+                Ah, Bh, _ = inputs.kappa_sweep(n, float(case), 0, shift=(z["u"], float(z["c"])))
+            hsh = hashlib.sha256()
+            hsh.update(Ah.tobytes(order="F"))
+            hsh.update(Bh.tobytes(order="F"))
+            if hsh.hexdigest() != str(z["sha256"]):
+                out[case] = {"error": "rebuilt inputs differ from the ones the oracle saw"}
+                continue
+            A, B = torch.from_numpy(Ah).to(dev), torch.from_numpy(Bh).to(dev)
+        ref = z["omega"]
+        res = {}
+        for prec, vec in (("fp64", False), ("mixed", True)):
+            for m in ("chol", "svd"):
+                try:
+                    om, _, _ = bse.solve(A, B, method=m, precision=prec, vectors=vec, handle=h)
+                    om = om.cpu().numpy()
+                except bse.BseError as e:
+                    res[f"{m}_{prec}"] = {"status": str(e)}
+                    continue
+                d = np.abs(om - ref)
+                res[f"{m}_{prec}"] = {"rel_err_smallest": float(d[0] / ref[0]), "normwise": float(d.max() / ref.max()),
+                                      "max_rel": float(np.max(d / ref))}
+        out[case] = res
+        del A, B
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_kernel_profile(args, local):
     import torch
 
@@ -508,6 +614,10 @@ def main():
     }
     if values_only:
         line["values_only"] = values_only
+    if not args.no_batched:
+        line["batched"] = batched_inline(dev, h, steps=max(1, min(args.steps, 3)), warmup=1)
+    if not args.no_accuracy:
+        line[f"accuracy_n{n}"] = accuracy_full_size(At, Bt, h, dev, seed_ok=(rank == 0))
     if sqrt_cmp:
         line["sqrt_vs_chol"] = sqrt_cmp
     if "mixed" in results and precs[0] != "mixed":

@@ -139,11 +139,14 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value);
  *          partial sums per level, FP64 recombination: the Ozaki scheme), so
  *          they carry FP64-level normwise error; pivots, matrix-vector
  *          products of the reductions, the tridiagonal solve and all
- *          element-wise work stay FP64.  With vectors, omega is then
- *          refined against the original A, B: omega_i becomes the Rayleigh
- *          quotient v_i^H Hcal1 v_i / v_i^H Sigma v_i of the pencil
- *          (Hcal1, Sigma) of Eq. (1) (second order in the vector error), and
- *          info->err_est reports the largest relative residual.
+ *          element-wise work stay FP64.  With vectors, the Cholesky and
+ *          square-root methods then refine omega against the original A, B:
+ *          omega_i becomes the Rayleigh quotient v_i^H Hcal1 v_i /
+ *          v_i^H Sigma v_i of the pencil (Hcal1, Sigma) of Eq. (1) (second
+ *          order in the vector error; it removes the omega^2 error of
+ *          Eq. (SquaredErr)).  The SVD method keeps its singular values,
+ *          which are relatively accurate where the quotient is accurate only
+ *          normwise.  info->err_est reports the largest relative residual.
  * omega    device, k doubles, ascending.
  * X, Y     device, n x k complex, leading dims ldx, ldy; both NULL for
  *          eigenvalues only.

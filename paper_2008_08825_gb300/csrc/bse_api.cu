@@ -460,7 +460,7 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
   TRY(gemm_z(s, p3));
   if (b.rf.F1) {
     StageScope scr(9, s);
-    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st));
+    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st, 1));
     return finish(h, s, st, info, b.rf.est_max);
   }
   return finish(h, s, st, info);
@@ -545,7 +545,10 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
   TRY(gemm_z(s, p2));
   if (b.rf.F1) {
     StageScope scr(9, s);
-    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st));
+    // Alg. 3's singular values keep their relative accuracy (the Golub-Kahan
+    // bisection); the Rayleigh quotient of the pencil is accurate only
+    // normwise, so for the SVD method omega stays and only the residuals go out
+    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st, 0));
     return finish(h, s, st, info, b.rf.est_max);
   }
   return finish(h, s, st, info);
@@ -645,7 +648,7 @@ static bse_status solve_sqrt_dev(bse_context* h, int64_t n, const cplx* A, int64
   TRY(gemm_z(s, p4));
   if (b.rf.F1) {
     StageScope scr(9, s);
-    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st));
+    TRY(refine_omega(s, n, k, b.rf.F1, b.rf.F2, X, ldx, Y, ldy, b.rf.work, omega, b.rf.est, b.rf.est_max, st, 1));
     return finish(h, s, st, info, b.rf.est_max);
   }
   return finish(h, s, st, info);

@@ -266,7 +266,7 @@ __global__ void sum_diff_kernel(int64_t n, int64_t k, const cplx* X, int64_t ldx
 __global__ void __launch_bounds__(256) refine_omega_kernel(int64_t n, const cplx* X, int64_t ldx, const cplx* Y,
                                                            int64_t ldy, const cplx* V1, const cplx* V2,
                                                            const cplx* P1, const cplx* P2, double* omega,
-                                                           double* est, const int64_t* status) {
+                                                           double* est, int replace, const int64_t* status) {
   __shared__ double red[8][8];
   if (*(volatile const int64_t*)status) return;
   const int64_t j = blockIdx.x;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) refine_omega_kernel(int64_t n, const cplx
       for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t[q] += red[q][ww];
     }
     est[j] = sqrt(t[3]) / (om * sqrt(t[4]));
-    omega[j] = 0.5 * (t[0] + t[1]) / t[2];
+    if (replace) omega[j] = 0.5 * (t[0] + t[1]) / t[2];
   }
 }
 
@@ -318,7 +318,7 @@ __global__ void max_kernel(int64_t k, const double* v, double* out) {
 
 bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, const cplx* M2, const cplx* X,
                         int64_t ldx, const cplx* Y, int64_t ldy, cplx* work, double* omega, double* est,
-                        double* est_max, const int64_t* status) {
+                        double* est_max, const int64_t* status, int replace) {
   if (n <= 0 || k <= 0) return BSE_OK;
   cplx* V1 = work;
   cplx* V2 = V1 + n * k;
@@ -336,7 +336,7 @@ bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, co
   GemmParams<cplx> b = gemm_params<cplx>(n, k, n, OPN, M2, n, OPN, V1, n, one, zero, P2, n);
   b.status = status;
   if ((r = gemm_z(s, b))) return r;
-  refine_omega_kernel<<<(unsigned)k, 256, 0, s>>>(n, X, ldx, Y, ldy, V1, V2, P1, P2, omega, est, status);
+  refine_omega_kernel<<<(unsigned)k, 256, 0, s>>>(n, X, ldx, Y, ldy, V1, V2, P1, P2, omega, est, replace, status);
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   max_kernel<<<1, 256, 0, s>>>(k, est, est_max);

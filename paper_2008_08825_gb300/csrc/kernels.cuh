@@ -31,9 +31,10 @@ bse_status finish_omega(cudaStream_t s, int64_t k, const double* lam, int mode, 
 // Mixed form: Rayleigh-quotient refinement of omega against the original
 // A, B (through full Hermitian M1 = A + B, M2 = A - B) and relative residuals.
 // work: 4 n k complex.  est: k doubles, est_max: 1 double (device).
+// replace = 0 keeps omega and only computes the residuals.
 bse_status refine_omega(cudaStream_t s, int64_t n, int64_t k, const cplx* M1, const cplx* M2, const cplx* X,
                         int64_t ldx, const cplx* Y, int64_t ldy, cplx* work, double* omega, double* est,
-                        double* est_max, const int64_t* status);
+                        double* est_max, const int64_t* status, int replace);
 // zero a complex matrix block
 bse_status zero_c(cudaStream_t s, int64_t m, int64_t n, cplx* A, int64_t lda);
 bse_status sqrt_factors(cudaStream_t s, int64_t n, const double* d, double* qp, double* qm, int64_t* status);
