@@ -118,7 +118,15 @@ typedef enum {
    * on one CTA.  Neither changes a result bit (the team splits work, not
    * sums).  Chosen per workload by the autotuner (autotune.py). */
   BSE_OPT_BATCH_TEAM = 5,
-  BSE_OPT_BATCH_TEAM_MIN_N = 6
+  BSE_OPT_BATCH_TEAM_MIN_N = 6,
+  /* Launch shapes (0 = the library default; autotune.py picks them per
+   * device and size): the Householder tridiagonalisation's matrix-vector
+   * kernel takes at most BSE_OPT_HEMV_ITEM_TILES row tiles per work item
+   * (1..16, default 8); the back-transformations split the k range of their
+   * thin V^H Z products into at most BSE_OPT_SPLITK_MAX layers (1..8,
+   * default 8).  Both change only the order of FP64 sums. */
+  BSE_OPT_HEMV_ITEM_TILES = 7,
+  BSE_OPT_SPLITK_MAX = 8
 } bse_option;
 bse_status bse_set_option(bse_handle h, int option, int64_t value);
 

@@ -157,6 +157,11 @@ class Handle:
         cycles (0 restores the default, about 1 s)."""
         _check(lib().bse_set_option(self._h, 4, int(value)))
 
+    def set_launch_shapes(self, hemv_item_tiles: int = 0, splitk_max: int = 0) -> None:
+        """Matvec row tiles per work item (1..16) and split-K cap (1..8); 0 = library default."""
+        _check(lib().bse_set_option(self._h, 7, int(hemv_item_tiles)))
+        _check(lib().bse_set_option(self._h, 8, int(splitk_max)))
+
     def set_batch_team(self, team: int, min_n: int | None = None) -> None:
         """Batched Alg. 2: CTAs per team (1, 2, 4, 8) for instances with n >= min_n."""
         _check(lib().bse_set_option(self._h, 5, int(team)))
@@ -205,6 +210,21 @@ def default_handle() -> Handle:
     return h
 
 
+def _default_tuned(n: int, precision: str) -> Handle:
+    """The default handle with the tuned launch shapes for this size and
+    precision applied (the autotuner's cache, else the table shipped for
+    GB300; the library defaults when neither has an entry)."""
+    from . import autotune
+
+    h = default_handle()
+    key = (autotune.size_bucket(n), precision)
+    if getattr(h, "_tuned_key", None) != key:
+        h.set_launch_shapes(0, 0)
+        h.tuning = autotune.apply_tuned(h, n, precision)
+        h._tuned_key = key
+    return h
+
+
 def _colmajor(A: torch.Tensor) -> torch.Tensor:
     if A.dtype != torch.complex128:
         raise TypeError("bse: A and B must be complex128")
@@ -226,7 +246,7 @@ def solve(A: torch.Tensor, B: torch.Tensor, method: str = "chol", precision: str
     il = 1 if il is None else int(il)
     iu = n if iu is None else int(iu)
     k = max(iu - il + 1, 0)
-    h = handle or default_handle()
+    h = handle or _default_tuned(n, precision)
     h.reserve(n, method, A.device, precision)
     Ac, Bc = _colmajor(A), _colmajor(B)
     omega = torch.empty(k, dtype=torch.float64, device=A.device)

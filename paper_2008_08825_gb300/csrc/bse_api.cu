@@ -54,6 +54,8 @@ struct bse_context {
   int64_t oz_wait = 0;  // 0: the engine's default wait limit
   int batch_cps = 1;
   int batch_team = 0;          // 0: the library default
+  int tune_hemv = 0;           // launch shapes (0: the library defaults)
+  int tune_splitk = 0;
   int64_t batch_team_min = 0;  // 0: the library default
 };
 
@@ -71,6 +73,12 @@ struct ProfGuard {
     }
     prof_set_current(nullptr);
   }
+};
+
+// Makes the handle's launch shapes current for one entry point.
+struct TuneGuard {
+  explicit TuneGuard(const bse_context* h) { tuning_set_current(LaunchTuning{h->tune_hemv, h->tune_splitk}); }
+  ~TuneGuard() { tuning_set_current(LaunchTuning{0, 0}); }
 };
 
 // Makes the tensor-core product workspace current for one solve (mixed form).
@@ -398,6 +406,7 @@ static bse_status solve_chol_dev(bse_context* h, int64_t n, const cplx* A, int64
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  TuneGuard tgd(h);
   ProfGuard pgd(h, s);
   // M1 = A + B (full), M2 = A - B (lower, in L)
   {
@@ -479,6 +488,7 @@ static bse_status solve_svd_dev(bse_context* h, int64_t n, const cplx* A, int64_
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  TuneGuard tgd(h);
   ProfGuard pgd(h, s);
   {
     StageScope sc(0, s);
@@ -573,6 +583,7 @@ static bse_status solve_sqrt_dev(bse_context* h, int64_t n, const cplx* A, int64
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  TuneGuard tgd(h);
   ProfGuard pgd(h, s);
   {
     StageScope sc(0, s);
@@ -666,6 +677,7 @@ static bse_status solve_tda_dev(bse_context* h, int64_t n, const cplx* A, int64_
   carve_tda(pl, b, n, k);
   int64_t* st = b.status;
   BSE_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), s));
+  TuneGuard tgd(h);
   ProfGuard pgd(h, s);
   {
     StageScope sc(0, s);
@@ -890,6 +902,7 @@ bse_status bse_grad(bse_handle h, int64_t n, int64_t k, const double* X, int64_t
   if (!dA || !dB || (k > 0 && (!X || !Y || !w))) return bse_internal_set_error("NULL pointer"), BSE_ERR_ARG;
   if (ldda < n || lddb < n || (k > 0 && (ldx < n || ldy < n))) return bse_internal_set_error("leading dimension < n"), BSE_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  TuneGuard tgd(h);
   ProfGuard pgd(h, s);
   StageScope sc(8, s);
   TRY(grad_outer(s, n, k, (const cplx*)X, ldx, (const cplx*)Y, ldy, w, (cplx*)dA, ldda, (cplx*)dB, lddb));
@@ -963,6 +976,16 @@ bse_status bse_set_option(bse_handle h, int option, int64_t value) {
     if (value < 0 || value > ((int64_t)1 << 36))
       return bse_internal_set_error("BSE_OPT_TC_WAIT_CYCLES must be in [0, 2^36]"), BSE_ERR_ARG;
     h->oz_wait = value;
+    return BSE_OK;
+  }
+  if (option == BSE_OPT_HEMV_ITEM_TILES) {
+    if (value < 0 || value > 16) return bse_internal_set_error("BSE_OPT_HEMV_ITEM_TILES must be in [0, 16]"), BSE_ERR_ARG;
+    h->tune_hemv = (int)value;
+    return BSE_OK;
+  }
+  if (option == BSE_OPT_SPLITK_MAX) {
+    if (value < 0 || value > 8) return bse_internal_set_error("BSE_OPT_SPLITK_MAX must be in [0, 8]"), BSE_ERR_ARG;
+    h->tune_splitk = (int)value;
     return BSE_OK;
   }
   if (option == BSE_OPT_BATCH_TEAM) {

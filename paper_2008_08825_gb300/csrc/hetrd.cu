@@ -51,20 +51,26 @@ static int device_sms() {
   return sms;
 }
 
+static thread_local LaunchTuning g_tuning = {0, 0};
+void tuning_set_current(const LaunchTuning& t) { g_tuning = t; }
+LaunchTuning tuning_current() { return g_tuning; }
+
 // Split-K layers for a product whose tiles do not fill the GPU: the count
-// s <= WSPLIT that brings tiles * s closest to whole waves of `slots` CTAs.
+// s <= WSPLIT (or the tuned cap) that brings tiles * s closest to whole
+// waves of `slots` CTAs.
 static int split_layers(int64_t tiles, int slots) {
   if (tiles >= 4 * slots) return 1;
+  const int cap = g_tuning.splitk_max > 0 && g_tuning.splitk_max < WSPLIT ? g_tuning.splitk_max : WSPLIT;
   int best = 1;
   double best_eff = 0.0;
-  for (int s = 1; s <= WSPLIT; ++s) {
+  for (int s = 1; s <= cap; ++s) {
     const double work = (double)tiles * s;
     const double eff = work / (slots * std::ceil(work / slots));
     if (eff > best_eff + 0.02) best = s, best_eff = eff;
   }
   return best;
 }
-constexpr int HR = 8;      // at most this many row tiles per CTA of the strip matvec
+constexpr int HR = 8;      // default: at most this many row tiles per work item of the strip matvec
 // partial-sum slots of the matvec: one per 32-wide column strip (row
 // products) plus one per chunk of row tiles (column products; at most one
 // per strip)
@@ -75,8 +81,9 @@ static inline int64_t hemv_slots(int64_t n) {
 // row tiles (64 x 32) per work item: up to HR, fewer while that leaves under
 // ~4 items per CTA (ntr^2 tiles in all, two CTAs per SM)
 static inline int hemv_chunk(int64_t ntr) {
+  const int64_t cap = g_tuning.hemv_items > 0 ? g_tuning.hemv_items : HR;
   const int64_t c = ntr * ntr / 1216;
-  return c < 1 ? 1 : (c > HR ? HR : (int)c);
+  return c < 1 ? 1 : (c > cap ? (int)cap : (int)c);
 }
 size_t hetrd_part_elems(int64_t n) {
   // partial-sum slots, norm and dot partials, and the matvec's per-column

@@ -140,6 +140,14 @@ bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, 
 int batched_team_default();
 int batched_team_min_n_default();
 
+// ---- launch shapes chosen per handle (autotuned), current for one solve ----
+struct LaunchTuning {
+  int hemv_items;  // tridiagonalisation matvec: at most this many row tiles per work item (1..16; 0: 8)
+  int splitk_max;  // back-transformations: at most this many split-K layers of V^H Z (1..8; 0: 8)
+};
+void tuning_set_current(const LaunchTuning& t);
+LaunchTuning tuning_current();
+
 // ---- ozgemm.cu ----  FP64-accurate complex GEMM on the BF16 tensor cores
 enum { OZ_ENGINE_TCGEN05 = 0, OZ_ENGINE_MMA_SYNC = 1 };
 struct OzWork {

@@ -11,6 +11,7 @@ Tolerances (the FP64 form; derivations in the comments):
 """
 import functools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -565,6 +566,48 @@ def test_mixed_tc_engines_agree(n, method, dev):
     tol = 1e-11 * o2.max() / _gaps(o2) + 1e-12
     err = np.maximum(np.abs(a - c).max(axis=0), np.abs(b - d).max(axis=0))
     assert np.all(err <= tol)
+
+
+@pytest.mark.parametrize("n,seed", [(257, 257), (2048, 0)])
+def test_launch_shapes_same_parity(n, seed, dev):
+    """The launch shapes the autotuner chooses among (row tiles per work item
+    of the tridiagonalisation's matvec, split-K cap of the back-transformation)
+    change only the order of FP64 sums: every choice passes the oracle gates
+    and agrees with the library default to rounding, in both forms."""
+    A, B = _base(n, seed)
+    om_r, X_r, Y_r = _oracle(n, seed)
+    for prec in ("fp64", "mixed"):
+        base = None
+        for shapes in [(0, 0), (1, 1), (2, 4), (16, 8)]:
+            h = bse.Handle()
+            h.set_launch_shapes(*shapes)
+            om, X, Y = _gpu(A, B, "chol", dev, precision=prec, handle=h)
+            assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+            assert sigma_residual(X, Y) <= 1e-10
+            _check_vectors(X, Y, X_r, Y_r, om_r)
+            if base is None:
+                base = om
+            assert np.max(np.abs(om - base) / base) <= 1e-13
+
+
+def test_tuned_table_applies(dev):
+    """bse.solve on the default handle applies the shipped (or cached) launch
+    shapes for the size, and the shipped table's entries are valid options."""
+    import json
+
+    from paper_2008_08825_gb300 import autotune
+
+    table = json.load(open(autotune.SHIPPED)) if os.path.exists(autotune.SHIPPED) else {}
+    for key, v in table.items():
+        if "/launch/" in key:
+            assert 1 <= v["hemv_item_tiles"] <= 16 and 1 <= v["splitk_max"] <= 8
+        if "/batched_team/" in key:
+            assert v["team"] in (1, 2, 4, 8) and v["min_n"] >= 1
+    A, B = _base(300, 8)
+    om, _, _ = _gpu(A, B, "chol", dev)
+    om_r, _, _ = oracle.solve_svd(A, B, vectors=False)
+    assert np.max(np.abs(om - om_r) / om_r) <= 1e-11
+    assert isinstance(bse.default_handle().tuning, dict)
 
 
 def test_autotuner_batched_and_threshold(dev, tmp_path, monkeypatch):
