@@ -111,7 +111,7 @@ typedef enum {
    * writes no output.  A tiny value forces that path (a test uses it); the
    * handle stays usable. */
   BSE_OPT_TC_WAIT_CYCLES = 4,
-  /* Batched Alg. 2: instances with n >= BSE_OPT_BATCH_TEAM_MIN_N (default
+  /* Batched solves: instances with n >= BSE_OPT_BATCH_TEAM_MIN_N (default
    * 448) are solved by a team of BSE_OPT_BATCH_TEAM CTAs (1, 2, 4 or 8;
    * default 4), one thread-block cluster on as many SMs, so the largest
    * instances do not set the batch's critical path; 1 puts every instance

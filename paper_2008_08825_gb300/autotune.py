@@ -7,7 +7,7 @@ Tunables:
   * back-transformations: the split-K cap of their thin V^H Z products;
   * mixed form: the m*n*k threshold above which complex products use the
     split-operand tensor-core engine instead of the FP64 FMA engine;
-  * batched Alg. 2: the team size (CTAs of one cluster per large instance)
+  * batched solves: the team size (CTAs of one cluster per large instance)
     and the size from which instances get a team;
   * batched persistent kernel without teams: resident CTAs per SM (1 or 2).
 
@@ -174,8 +174,8 @@ def tune_launch_shapes(A: torch.Tensor, B: torch.Tensor, handle: "bse.Handle", p
 def tune_batched_teams(batch: "bse.Batch", handle: "bse.Handle",
                        candidates=((1, 448), (2, 448), (4, 320), (4, 448), (4, 640), (8, 640)),
                        force: bool = False) -> dict:
-    """Pick the team size and threshold of batched Alg. 2 for this batch class."""
-    key = f"{_device_key()}/batched_team/{batch_class(batch.n)}/k{batch.k}"
+    """Pick the team size and threshold of a batched solve for this method and batch class."""
+    key = f"{_device_key()}/batched_team/{batch.method}/{batch_class(batch.n)}/k{batch.k}"
     cached = None if force else _load().get(key)
     if cached is None:
         times = {}
@@ -206,7 +206,7 @@ def apply_tuned(handle: "bse.Handle", n: int, precision: str = "fp64") -> dict:
 
 
 def apply_tuned_batched(handle: "bse.Handle", batch: "bse.Batch") -> dict:
-    cached = lookup(f"{_device_key()}/batched_team/{batch_class(batch.n)}/k{batch.k}")
+    cached = lookup(f"{_device_key()}/batched_team/{batch.method}/{batch_class(batch.n)}/k{batch.k}")
     if not cached:
         return {}
     handle.set_batch_team(cached["team"], cached["min_n"])
@@ -241,8 +241,9 @@ def main():
     for i in range(len(sizes)):
         A, B = inputs.base(int(sizes[i]), seed=i)
         inst.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
-    bt = bse.Batch(inst, k=32, method="chol")
-    print("teams", tune_batched_teams(bt, h, force=True), flush=True)
+    for method in ("chol", "svd"):
+        bt = bse.Batch(inst, k=32, method=method)
+        print("teams", method, tune_batched_teams(bt, h, force=True), flush=True)
 
 
 if __name__ == "__main__":

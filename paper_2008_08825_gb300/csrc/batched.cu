@@ -20,16 +20,15 @@
 //   the k smallest singular values; twisted-factorisation vectors split into
 //   U_B, V_B; one Newton-Schulz step on each; U = Q U_B, V = P V_B one
 //   reflector at a time; X, Y from L1 U and L2 V through the fused epilogue.
-// The Cholesky method's large instances (n >= BATCH_TEAM_MIN_N) are solved by
-// a team: the CTAs of one thread-block cluster (BATCH_TEAM CTAs on as many
-// SMs).  The team splits the heavy stages -- the Cholesky panels and
-// trailing updates, both congruence products (by output tiles), and every
-// column of the Householder tridiagonalisation (matrix-vector rows, rank-2
-// update columns; the new w is exchanged through distributed shared memory)
-// -- and meets at cluster barriers between dependent steps; the cheap k-sized
-// tail (bisection, vectors, back-transformation, X and Y) runs on the team's
-// first CTA.  Without teams a whole instance stays on one SM; the only global
-// atomics are the queue counters.
+// Large instances (n >= BATCH_TEAM_MIN_N) are solved by a team: the CTAs of
+// one thread-block cluster (BATCH_TEAM CTAs on as many SMs).  The team splits
+// the heavy stages -- the Cholesky panels and trailing updates and the
+// congruence / G products (by output tiles), every column of the Householder
+// tridiagonalisation or bidiagonalisation (matrix-vector rows, update
+// columns; the vector each step needs whole is exchanged through
+// distributed shared memory) -- and the k-sized tail by eigenpairs, and
+// meets at cluster barriers between dependent steps.  Without teams a whole
+// instance stays on one SM; the only global atomics are the queue counters.
 #include <float.h>
 
 #include <atomic>
@@ -600,11 +599,17 @@ __device__ __forceinline__ void house_params(cplx alpha, double xn2, cplx* tau, 
 
 // unblocked bidiagonalisation of G (n x n, ld n): left reflector u_i kept in
 // G(i:, i) (unit first entry), right reflector v_i in Vr(i+1:, i)
+// In a team every CTA forms u and v (the left and right reflectors) in its
+// own shared memory from the same column / row; the updates are split by
+// columns, t = tau G v by rows (each CTA storing its rows of t into every
+// member's `ts`); the first CTA writes u, v, the taus, d and e after the
+// team has read what they overwrite.
 __device__ void cta_gebrd(int64_t n, cplx* G, cplx* Vr, cplx* tauq, cplx* taup, double* d, double* e, cplx* ts,
-                          double* red) {
+                          double* red, cplx* us, cplx* vrs, Team tm = Team{0, 1}) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ cplx h_tau, h_scal;
   __shared__ double h_beta;
+  const int64_t cstride = (int64_t)tm.size * (BT / 32);
   for (int64_t i = 0; i < n; ++i) {
     // left reflector on G(i:, i)
     double nrm = 0.0;
@@ -615,26 +620,29 @@ __device__ void cta_gebrd(int64_t n, cplx* G, cplx* Vr, cplx* tauq, cplx* taup, 
       double b;
       house_params(G[IDX2(i, i, n)], nrm, &t, &sc, &b);
       h_tau = t, h_scal = sc, h_beta = b;
-      tauq[i] = t;
-      d[i] = b;
+      if (tm.rank == 0) {
+        tauq[i] = t;
+        d[i] = b;
+      }
     }
     __syncthreads();
-    for (int64_t r = i + tid; r < n; r += BT)
-      G[IDX2(r, i, n)] = (r == i) ? mkc(1.0, 0.0) : cmul(G[IDX2(r, i, n)], h_scal);
+    for (int64_t r = i + tid; r < n; r += BT) us[r - i] = (r == i) ? mkc(1.0, 0.0) : cmul(G[IDX2(r, i, n)], h_scal);
     __syncthreads();
     // G(i:, c) -= conj(tau) u (u^H G(i:, c)), c > i: warp per column
     const cplx ctau = cconj(h_tau);
-    for (int64_t c = i + 1 + warp; c < n; c += BT / 32) {
+    for (int64_t c = i + 1 + tm.rank + (int64_t)tm.size * warp; c < n; c += cstride) {
       cplx sdot = mkc(0.0, 0.0);
-      for (int64_t r = i + lane; r < n; r += 32) cfma_cj(sdot, G[IDX2(r, i, n)], G[IDX2(r, c, n)]);
+      for (int64_t r = i + lane; r < n; r += 32) cfma_cj(sdot, us[r - i], G[IDX2(r, c, n)]);
       for (int o = 16; o > 0; o >>= 1) {
         sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o);
         sdot.y += __shfl_xor_sync(0xffffffffu, sdot.y, o);
       }
       const cplx f = cmul(ctau, sdot);
-      for (int64_t r = i + lane; r < n; r += 32) G[IDX2(r, c, n)] = csub(G[IDX2(r, c, n)], cmul(G[IDX2(r, i, n)], f));
+      for (int64_t r = i + lane; r < n; r += 32) G[IDX2(r, c, n)] = csub(G[IDX2(r, c, n)], cmul(us[r - i], f));
     }
-    __syncthreads();
+    team_sync(tm);
+    if (tm.rank == 0)
+      for (int64_t r = i + tid; r < n; r += BT) G[IDX2(r, i, n)] = us[r - i];
     if (i + 1 >= n) break;
     // right reflector from x = conj(G(i, i+1:))
     nrm = 0.0;
@@ -645,36 +653,55 @@ __device__ void cta_gebrd(int64_t n, cplx* G, cplx* Vr, cplx* tauq, cplx* taup, 
       double b;
       house_params(cconj(G[IDX2(i, i + 1, n)]), nrm, &t, &sc, &b);
       h_tau = t, h_scal = sc, h_beta = b;
-      taup[i] = t;
-      e[i] = b;
+      if (tm.rank == 0) {
+        taup[i] = t;
+        e[i] = b;
+      }
     }
     __syncthreads();
-    for (int64_t c = i + 1 + tid; c < n; c += BT)
-      Vr[IDX2(c, i, n)] = (c == i + 1) ? mkc(1.0, 0.0) : cmul(cconj(G[IDX2(i, c, n)]), h_scal);
+    for (int64_t c = i + 1 + tid; c < n; c += BT) {
+      const cplx v = (c == i + 1) ? mkc(1.0, 0.0) : cmul(cconj(G[IDX2(i, c, n)]), h_scal);
+      vrs[c - i - 1] = v;
+      if (tm.rank == 0) Vr[IDX2(c, i, n)] = v;
+    }
     __syncthreads();
-    // G(i+1:, i+1:) <- G - tau (G v) v^H: t = G v by rows, then warp per column
-    for (int64_t r = i + 1 + tid; r < n; r += BT) {
+    // G(i+1:, i+1:) <- G - tau (G v) v^H: t = G v by rows (this CTA's rows),
+    // then warp per column
+    const int64_t m = n - i - 1, per = (m + tm.size - 1) / tm.size, rb0 = tm.rank * per;
+    const int64_t rb1 = rb0 + per < m ? rb0 + per : m;
+    for (int64_t rr = rb0 + tid; rr < rb1; rr += BT) {
+      const int64_t r = i + 1 + rr;
       cplx acc = mkc(0.0, 0.0);
-      for (int64_t c = i + 1; c < n; ++c) cfma(acc, G[IDX2(r, c, n)], Vr[IDX2(c, i, n)]);
-      ts[r - i - 1] = cmul(h_tau, acc);
+      for (int64_t c = i + 1; c < n; ++c) cfma(acc, G[IDX2(r, c, n)], vrs[c - i - 1]);
+      const cplx tr = cmul(h_tau, acc);
+      if (tm.size > 1) {
+        for (int q = 0; q < tm.size; ++q) cg::this_cluster().map_shared_rank(ts, q)[rr] = tr;
+      } else {
+        ts[rr] = tr;
+      }
     }
-    __syncthreads();
-    for (int64_t c = i + 1 + warp; c < n; c += BT / 32) {
-      const cplx vc = cconj(Vr[IDX2(c, i, n)]);
+    team_sync(tm);
+    for (int64_t c = i + 1 + tm.rank + (int64_t)tm.size * warp; c < n; c += cstride) {
+      const cplx vc = cconj(vrs[c - i - 1]);
       for (int64_t r = i + 1 + lane; r < n; r += 32) G[IDX2(r, c, n)] = csub(G[IDX2(r, c, n)], cmul(ts[r - i - 1], vc));
     }
-    __syncthreads();
+    team_sync(tm);
   }
 }
 
-__device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cplx* S, cplx* Iv, int* flag) {
+// A team splits Alg. 3 as it splits Alg. 2: the Choleskys, G = L1^H L2 and
+// the bidiagonalisation by tiles, columns and rows, the k-sized tail by
+// singular triplets (triplet t on CTA t % size).  us, vrs: two n-entry
+// shared buffers of the bidiagonalisation (S and Iv are free by then).
+__device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cplx* S, cplx* Iv, int* flag,
+                                   cplx* us, Team tm = Team{0, 1}) {
   const int64_t n = D.n, k = D.k;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   SvdWs w;
   carve_svd_inst(D.ws, n, k, &w);
   int64_t* st = D.status;
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
-  for (int64_t q = tid; q < n * n; q += BT) {
+  for (int64_t q = tm.rank * BT + tid; q < n * n; q += (int64_t)tm.size * BT) {
     const int64_t i = q % n, j = q / n;
     if (i >= j) {
       const cplx a = D.A[IDX2(i, j, n)], b = D.B[IDX2(i, j, n)];
@@ -683,34 +710,36 @@ __device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cp
     }
   }
   __threadfence_block();
-  __syncthreads();
-  if (!cta_potrf(n, w.L1, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_APLUSB)) return;
-  if (!cta_potrf(n, w.L2, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_AMINUSB)) return;
+  team_sync(tm);
+  if (!cta_potrf(n, w.L1, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_APLUSB, tm)) return;
+  if (!cta_potrf(n, w.L2, w.Linv, st, S, Iv, flag, BSE_ERR_NOT_PD_AMINUSB, tm)) return;
   // G = L1^H L2
   GemmParams<cplx> pg = gemm_params<cplx>(n, n, n, OPC, w.L1, n, OPN, w.L2, n, one, zero, w.G, n);
   pg.triA = TRI_UP;
   pg.triB = TRI_LO;
-  gemm_cta<cplx, 8>(pg);
+  gemm_team<cplx, 8>(pg, tm);
   __threadfence_block();
-  __syncthreads();
-  cta_gebrd(n, w.G, w.Vr, w.tauq, w.taup, w.d, w.e, vs, red);
+  team_sync(tm);
+  cta_gebrd(n, w.G, w.Vr, w.tauq, w.taup, w.d, w.e, vs, red, us, S, tm);
   // Golub-Kahan tridiagonal (zero diagonal), size N = 2n
   const int64_t N = 2 * n;
   double tn = 0.0, em = 0.0;
   for (int64_t i = tid; i < N - 1; i += BT) {
     const double o = (i & 1) ? w.e[i >> 1] : w.d[i >> 1];
-    w.off[i] = o;
-    w.e2[i] = o * o;
+    if (tm.rank == 0) {
+      w.off[i] = o;
+      w.e2[i] = o * o;
+    }
     tn = fmax(tn, 2.0 * fabs(o));
     em = fmax(em, o * o);
   }
   tn = cta_max(tn, red);
   em = cta_max(em, red);
   __threadfence_block();
-  __syncthreads();
+  team_sync(tm);
   const double pivmin = DBL_MIN * fmax(1.0, em), g = DBL_EPSILON * fmax(tn, DBL_MIN);
   const double lo0 = -tn - 4.0 * pivmin, hi0 = tn + 4.0 * pivmin;
-  for (int64_t t = tid; t < k; t += BT) {
+  for (int64_t t = tm.rank + (int64_t)tm.size * tid; t < k; t += (int64_t)tm.size * BT) {
     const int tt = (int)(n + t);  // the (t+1)-th smallest positive eigenvalue of TGK
     double a = lo0, b = hi0;
     for (int it = 0; it < 256; ++it) {
@@ -775,12 +804,14 @@ __device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cp
     w.c1[t] = 1.0 / sqrt(l);
   }
   __threadfence_block();
-  __syncthreads();
-  if (st[0]) return;
-  // Newton-Schulz on U_B and V_B (k x k Gram, plain loops)
+  team_sync(tm);
+  if (st[0]) return;  // the same word for every member
+  // Newton-Schulz on U_B and V_B (k x k Gram, plain loops); from the update
+  // on a member works on its own columns c = rank, rank + size, ...
+  const int64_t kc = (k - tm.rank + tm.size - 1) / tm.size;
   for (int pass = 0; pass < 2; ++pass) {
     double* Zm = pass == 0 ? w.UB : w.VB;
-    for (int64_t q = tid; q < k * k; q += BT) {
+    for (int64_t q = tm.rank * BT + tid; q < k * k; q += (int64_t)tm.size * BT) {
       const int64_t a = q % k, b = q / k;
       if (a < b) continue;
       double s2 = 0.0;
@@ -790,22 +821,25 @@ __device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cp
       w.E[b + a * k] = s2;
     }
     __threadfence_block();
-    __syncthreads();
-    for (int64_t q = tid; q < n * k; q += BT) {
-      const int64_t i = q % n, c = q / n;
+    team_sync(tm);
+    for (int64_t q = tid; q < n * kc; q += BT) {
+      const int64_t i = q % n, c = tm.rank + (q / n) * tm.size;
       double s2 = 0.0;
       for (int64_t b = 0; b < k; ++b) s2 = fma(Zm[i + b * n], w.E[b + c * k], s2);
-      w.sc[q] = Zm[q] - 0.5 * s2;
+      w.sc[i + c * n] = Zm[i + c * n] - 0.5 * s2;
     }
     __threadfence_block();
     __syncthreads();
     cplx* out = pass == 0 ? w.Uc : w.Vc;
-    for (int64_t q = tid; q < n * k; q += BT) out[q] = mkc(w.sc[q], 0.0);
+    for (int64_t q = tid; q < n * kc; q += BT) {
+      const int64_t i = q % n, c = tm.rank + (q / n) * tm.size;
+      out[i + c * n] = mkc(w.sc[i + c * n], 0.0);
+    }
     __threadfence_block();
-    __syncthreads();
+    team_sync(tm);  // E is rewritten by the next pass
   }
   // back-transformations: U = H_L(0) ... H_L(n-1) U_B, V = H_R(0) ... H_R(n-2) V_B
-  for (int64_t c = warp; c < k; c += BT / 32) {
+  for (int64_t c = tm.rank + (int64_t)tm.size * warp; c < k; c += (int64_t)tm.size * (BT / 32)) {
     cplx* uc = w.Uc + c * n;
     for (int64_t j = n - 1; j >= 0; --j) {
       const cplx* u = w.G + IDX2(j, j, n);
@@ -836,18 +870,18 @@ __device__ void solve_instance_svd(const BatchDesc& D, cplx* vs, double* red, cp
     }
   }
   __threadfence_block();
-  __syncthreads();
+  team_sync(tm);
   // T1 = L1 U; X, Y from T1 and L2 V, c1 = c2 = omega^{-1/2}
   GemmParams<cplx> p1 = gemm_params<cplx>(n, k, n, OPN, w.L1, n, OPN, w.Uc, n, one, zero, w.T1, n);
   p1.triA = TRI_LO;
-  gemm_cta<cplx, 8>(p1);
+  gemm_team<cplx, 8>(p1, tm);
   __threadfence_block();
-  __syncthreads();
+  team_sync(tm);
   GemmParams<cplx> p2 = gemm_params<cplx>(n, k, n, OPN, w.L2, n, OPN, w.Vc, n, one, zero, D.X, n);
   p2.triA = TRI_LO;
   p2.epi = EPI_XY;
   p2.P = w.T1, p2.ldp = n, p2.c1 = w.c1, p2.c2 = w.c1, p2.Y = D.Y, p2.ldy = n;
-  gemm_cta<cplx, 8>(p2);
+  gemm_team<cplx, 8>(p2, tm);
 }
 
 __global__ void __launch_bounds__(BT, 1) batched_svd_kernel(const BatchDesc* __restrict__ desc, int64_t count,
@@ -864,7 +898,7 @@ __global__ void __launch_bounds__(BT, 1) batched_svd_kernel(const BatchDesc* __r
     const int idx = next;
     __syncthreads();
     if (idx >= count) break;
-    solve_instance_svd(desc[idx], vs, red, S, Iv, &flag);
+    solve_instance_svd(desc[idx], vs, red, S, Iv, &flag, dyn + 1024);
     __syncthreads();
   }
 }
@@ -889,12 +923,13 @@ __global__ void __launch_bounds__(BT, 1) batched_chol_kernel(const BatchDesc* __
   }
 }
 
-// Alg. 2 with teams: the clusters (BATCH_TEAM CTAs each) take the first
-// `nbig` instances of the size-ordered queue one at a time, a team per
-// instance; when none is left, every CTA takes the remaining (small)
-// instances alone from a second counter.
-__global__ void __launch_bounds__(BT, 1) batched_chol_team_kernel(const BatchDesc* __restrict__ desc, int64_t count,
-                                                                  int64_t nbig, int* counters) {
+// With teams: the clusters take the first `nbig` instances of the
+// size-ordered queue one at a time, a team per instance; when none is left,
+// every CTA takes the remaining (small) instances alone from a second
+// counter.  METHOD: BSE_METHOD_CHOL (Alg. 2) or BSE_METHOD_SVD (Alg. 3).
+template <int METHOD>
+__global__ void __launch_bounds__(BT, 1) batched_team_kernel(const BatchDesc* __restrict__ desc, int64_t count,
+                                                             int64_t nbig, int* counters) {
   extern __shared__ cplx dyn[];
   cplx* vs = dyn;                    // 1024
   cplx* wsv = dyn + 1024;            // 1024
@@ -913,7 +948,10 @@ __global__ void __launch_bounds__(BT, 1) batched_chol_team_kernel(const BatchDes
     const int idx = next;
     cl.sync();
     if (idx >= nbig) break;
-    solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag, tm);
+    if (METHOD == BSE_METHOD_SVD)
+      solve_instance_svd(desc[idx], vs, red, S, Iv, &flag, wsv, tm);
+    else
+      solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag, tm);
     __syncthreads();
   }
   for (;;) {
@@ -922,7 +960,10 @@ __global__ void __launch_bounds__(BT, 1) batched_chol_team_kernel(const BatchDes
     const int idx = next;
     __syncthreads();
     if (idx >= count) break;
-    solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag);
+    if (METHOD == BSE_METHOD_SVD)
+      solve_instance_svd(desc[idx], vs, red, S, Iv, &flag, wsv);
+    else
+      solve_instance(desc[idx], vs, wsv, red, S, Iv, &flag);
     __syncthreads();
   }
 }
@@ -933,8 +974,8 @@ int batched_team_default() { return BATCH_TEAM; }
 int batched_team_min_n_default() { return BATCH_TEAM_MIN_N; }
 
 // Largest grid of whole teams of `team` CTAs that can be resident at once
-// (0: none), looked up once per device and team size.
-static int team_grid_query(size_t smem, int team) {
+// (0: none), looked up once per device, method and team size.
+static int team_grid_query(const void* kern, size_t smem, int team) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -945,26 +986,28 @@ static int team_grid_query(size_t smem, int team) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, (void*)batched_chol_team_kernel, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return clusters * team;
 }
 
-static int team_grid(size_t smem, int team) {
+static int team_grid(int method, size_t smem, int team) {
   constexpr int kMaxDev = 64;
-  static std::atomic<int> grid_of[kMaxDev][4];  // grid + 1 per team size 1, 2, 4, 8 (0: not yet looked up)
-  const int slot = team == 8 ? 3 : team == 4 ? 2 : team == 2 ? 1 : 0;
+  // grid + 1 per method and team size 1, 2, 4, 8 (0: not yet looked up)
+  static std::atomic<int> grid_of[kMaxDev][2][4];
+  const int slot = team == 8 ? 3 : team == 4 ? 2 : team == 2 ? 1 : 0, ms = method == BSE_METHOD_SVD ? 1 : 0;
+  const void* kern = ms ? (const void*)batched_team_kernel<BSE_METHOD_SVD> : (const void*)batched_team_kernel<BSE_METHOD_CHOL>;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
-    return team_grid_query(smem, team);
+    return team_grid_query(kern, smem, team);
   }
-  int g = grid_of[dev][slot].load(std::memory_order_relaxed);
+  int g = grid_of[dev][ms][slot].load(std::memory_order_relaxed);
   if (!g) {
-    g = team_grid_query(smem, team) + 1;
-    grid_of[dev][slot].store(g, std::memory_order_relaxed);
+    g = team_grid_query(kern, smem, team) + 1;
+    grid_of[dev][ms][slot].store(g, std::memory_order_relaxed);
   }
   return g - 1;
 }
@@ -974,10 +1017,11 @@ bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, 
   const size_t smem = batched_smem_bytes();
   bse_status r = set_smem_attr((const void*)batched_chol_kernel, (int)smem);
   if (!r) r = set_smem_attr((const void*)batched_svd_kernel, (int)smem);
-  if (!r) r = set_smem_attr((const void*)batched_chol_team_kernel, (int)smem);
+  if (!r) r = set_smem_attr((const void*)batched_team_kernel<BSE_METHOD_CHOL>, (int)smem);
+  if (!r) r = set_smem_attr((const void*)batched_team_kernel<BSE_METHOD_SVD>, (int)smem);
   if (r) return r;
   BSE_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
-  const int tgrid = (method == BSE_METHOD_CHOL && nbig > 0 && team > 1) ? team_grid(smem, team) : 0;
+  const int tgrid = (nbig > 0 && team > 1) ? team_grid(method, smem, team) : 0;
   if (tgrid > 0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -989,7 +1033,12 @@ bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, 
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    BSE_CUDA(cudaLaunchKernelEx(&cfg, batched_chol_team_kernel, (const BatchDesc*)desc, count, nbig, counter));
+    if (method == BSE_METHOD_SVD)
+      BSE_CUDA(cudaLaunchKernelEx(&cfg, batched_team_kernel<BSE_METHOD_SVD>, (const BatchDesc*)desc, count, nbig,
+                                  counter));
+    else
+      BSE_CUDA(cudaLaunchKernelEx(&cfg, batched_team_kernel<BSE_METHOD_CHOL>, (const BatchDesc*)desc, count, nbig,
+                                  counter));
   } else if (method == BSE_METHOD_SVD) {
     batched_svd_kernel<<<grid, BT, smem, s>>>((const BatchDesc*)desc, count, counter);
   } else {

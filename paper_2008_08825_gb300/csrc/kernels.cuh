@@ -133,8 +133,8 @@ cudaError_t single_chol_prepare();
 cudaError_t single_chol_launch(cudaStream_t s, int64_t n, int64_t k, const void* A, const void* B, double* omega,
                                void* X, void* Y, char* ws, int64_t* status);
 // counter: two ints (queue counters); nbig: the first nbig instances of the
-// size-ordered table are solved by teams of `team` CTAs (Alg. 2 only; team 1
-// or nbig 0: every instance on one CTA)
+// size-ordered table are solved by teams of `team` CTAs (team 1 or nbig 0:
+// every instance on one CTA)
 bse_status batched_chol_launch(cudaStream_t s, const void* desc, int64_t count, int* counter, int grid,
                                int method, int64_t nbig, int team);
 int batched_team_default();

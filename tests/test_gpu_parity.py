@@ -268,10 +268,11 @@ def test_batched_persistent_kernel_vs_oracle(dev, method):
         assert np.linalg.norm(S) <= 1e-10
 
 
-def test_batched_teams_bit_identical(dev):
-    """Large Alg. 2 instances are solved by a team of CTAs (one cluster); the
-    team splits work, not sums, so every team size gives the same bits, and
-    the results match the oracle."""
+@pytest.mark.parametrize("method", ["chol", "svd"])
+def test_batched_teams_bit_identical(dev, method):
+    """Large instances are solved by a team of CTAs (one cluster); the team
+    splits work, not sums, so every team size gives the same bits, and the
+    results match the oracle."""
     sizes = inputs.batched_sizes()
     order = np.argsort(-sizes)
     idx = list(order[:6]) + [int(np.argmin(sizes)), 3, 4]
@@ -280,7 +281,7 @@ def test_batched_teams_bit_identical(dev):
     outs = []
     for team in (1, 2, 4, 8):
         h.set_batch_team(team, 64)
-        bt = bse.Batch(inst, k=32, method="chol").run(handle=h)
+        bt = bse.Batch(inst, k=32, method=method).run(handle=h)
         assert all(s == 0 for s in bt.status)
         outs.append([(o.clone(), X.clone(), Y.clone()) for o, X, Y in bt.results()])
     for other in outs[1:]:
