@@ -110,18 +110,33 @@ __device__ __forceinline__ cplx block_sum_c(cplx v, double* red) {
   return mkc(a, b);
 }
 
-// 1. column update + norm partial sums of rows >= j+2
+// 1. column update + norm partial sums of rows >= j+2.  With nfin > 0 it
+// also finishes the previous column's w (step 4 below, w += alpha v with
+// alpha = -tau/2 (w^H v) from nfin partial sums): every CTA forms alpha, uses
+// the finished w and stores it for its rows > j (row j is read by every CTA
+// and needed by no later step, so it is left as it was).
 __global__ void __launch_bounds__(RB) tr_col_update(int64_t n, int64_t p, int64_t j, cplx* __restrict__ A,
                                                     int64_t lda, const cplx* __restrict__ V, int64_t ldv,
-                                                    const cplx* __restrict__ W, int64_t ldw, double* __restrict__ d,
-                                                    double* __restrict__ npart, const int64_t* status) {
+                                                    cplx* __restrict__ W, int64_t ldw, double* __restrict__ d,
+                                                    double* __restrict__ npart, const double* __restrict__ dpart,
+                                                    int nfin, const cplx* __restrict__ tau, const int64_t* status) {
   __shared__ cplx vj[NBT], wj[NBT];
+  __shared__ cplx falpha;
   __shared__ double red[32];
   if (*(volatile const int64_t*)status) return;
   const int jj = (int)(j - p);
+  const bool fin = nfin > 0 && jj > 0;
+  if (fin && threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nfin; ++i) a += dpart[2 * i], b += dpart[2 * i + 1];
+    falpha = cscale(cmul(tau[j - 1], mkc(a, b)), -0.5);
+  }
+  __syncthreads();
   if (threadIdx.x < jj) {
     vj[threadIdx.x] = V[IDX2(j, p + threadIdx.x, ldv)];
-    wj[threadIdx.x] = W[IDX2(j, threadIdx.x, ldw)];
+    cplx w0 = W[IDX2(j, threadIdx.x, ldw)];
+    if (fin && threadIdx.x == jj - 1) w0 = cadd(w0, cmul(falpha, V[IDX2(j, j - 1, ldv)]));
+    wj[threadIdx.x] = w0;
   }
   __syncthreads();
   const int64_t r = j + (int64_t)blockIdx.x * RB + threadIdx.x;
@@ -130,7 +145,12 @@ __global__ void __launch_bounds__(RB) tr_col_update(int64_t n, int64_t p, int64_
     cplx c = A[IDX2(r, j, lda)];
     for (int q = 0; q < jj; ++q) {
       // c -= V(r,q) conj(W(j,q)) + W(r,q) conj(V(j,q))
-      const cplx vr = V[IDX2(r, p + q, ldv)], wr = W[IDX2(r, q, ldw)];
+      const cplx vr = V[IDX2(r, p + q, ldv)];
+      cplx wr = W[IDX2(r, q, ldw)];
+      if (fin && q == jj - 1) {
+        wr = cadd(wr, cmul(falpha, V[IDX2(r, j - 1, ldv)]));
+        if (r > j) W[IDX2(r, q, ldw)] = wr;
+      }
       const cplx a = cmul(vr, cconj(wj[q])), b = cmul(wr, cconj(vj[q]));
       c = csub(c, cadd(a, b));
     }
@@ -452,10 +472,11 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
   const cplx one = mkc(1.0, 0.0), mone = mkc(-1.0, 0.0);
   for (int64_t p = 0; p < n - 1; p += NBT) {
     const int64_t bs = (n - 1 - p) < NBT ? (n - 1 - p) : NBT;
+    int nfin = 0;  // partial sums of the previous column's w^H v still to fold in
     for (int64_t j = p; j < p + bs; ++j) {
       const int64_t m = n - j - 1;  // length of the reflector
       const unsigned g1 = ceil_div_u(n - j, RB);
-      LAUNCH(tr_col_update, g1, RB, n, p, j, A, lda, w.V, ldv, w.W, ldw, w.d, npart, status);
+      LAUNCH(tr_col_update, g1, RB, n, p, j, A, lda, w.V, ldv, w.W, ldw, w.d, npart, dpart, nfin, w.tau, status);
       const unsigned g2 = ceil_div_u(m, RB);
       LAUNCH(tr_house, g2, RB, n, j, A, lda, w.V, ldv, w.tau, w.e, npart, (int)g1, status);
       const int64_t nst = (m + HS - 1) / HS, ntr = (m + HT - 1) / HT;  // strips, row tiles
@@ -476,7 +497,11 @@ bse_status hetrd_lower(cudaStream_t s, int64_t n, cplx* A, int64_t lda, const He
       const unsigned ga = ceil_div_u(m, AR);
       LAUNCH(tr_w_assemble, ga, 256, n, p, j, w.V, ldv, w.W, ldw, part, ldpart, (int)nst, hr, s12, w.tau, dpart,
              status);
-      LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)ga, status);
+      if (j + 1 < p + bs) {
+        nfin = (int)ga;  // the next column update finishes this w
+      } else {
+        LAUNCH(tr_w_finish, g2, RB, n, p, j, w.V, ldv, w.W, ldw, w.tau, dpart, (int)ga, status);
+      }
     }
     const int64_t t0 = p + bs, mt = n - t0;
     if (mt > 0 && p + 2 * bs <= n) {
