@@ -127,13 +127,22 @@ __global__ void tri_grid_kernel(int64_t N, const double* __restrict__ a, const d
   cnt[g] = sturm_count(a, e2, 0, (int)N, x, prm[0]);
 }
 
+// Multisection: TRI_MS consecutive lanes of a warp share one eigenvalue and
+// evaluate Sturm counts at TRI_MS interior points of its interval in each
+// round, which shrinks it by TRI_MS + 1 (log2(5) bits per round instead of
+// one).  The FP64 pipe is the bound of a Sturm step (a division per entry);
+// one lane per eigenvalue leaves it mostly idle, four keep it busy.
+constexpr int TRI_MS = 4;
 __global__ void tri_bisect_kernel(int64_t total, const double* __restrict__ a, const double* __restrict__ e2,
                                   const int* __restrict__ bstart, const int* __restrict__ iprm,
                                   const double* __restrict__ prm, int mode, double* __restrict__ lam,
                                   int* __restrict__ blk, const int* __restrict__ cnt, const int64_t* status) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= total) return;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t s = gt / TRI_MS;
+  const int sub = (int)(gt % TRI_MS);
+  if (s >= total) return;  // the whole group of TRI_MS lanes
   if (*(volatile const int64_t*)status) return;
+  const unsigned gmask = ((1u << TRI_MS) - 1u) << ((threadIdx.x & 31) & ~(TRI_MS - 1));
   const int nb = iprm[0];
   const int b = find_block(bstart, nb, s, mode);
   const int b0 = bstart[b], b1 = bstart[b + 1];
@@ -154,14 +163,25 @@ __global__ void tri_bisect_kernel(int64_t total, const double* __restrict__ a, c
     lo = glo;
     hi = ghi;
   }
-  for (int it = 0; it < 256; ++it) {
-    const double mid = 0.5 * (lo + hi);
+  for (int it = 0; it < 128; ++it) {
     const double w = hi - lo;
-    if (w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || w <= 4.0 * pivmin || mid == lo || mid == hi) break;
-    if (sturm_count(a, e2, b0, b1, mid, pivmin) > t) hi = mid; else lo = mid;
+    const double x0 = lo + w * (1.0 / (TRI_MS + 1)), xl = lo + w * ((double)TRI_MS / (TRI_MS + 1));
+    if (w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || w <= 4.0 * pivmin || x0 <= lo || xl >= hi) break;
+    const double x = lo + w * ((double)(sub + 1) / (TRI_MS + 1));
+    const unsigned above = __ballot_sync(gmask, sturm_count(a, e2, b0, b1, x, pivmin) > t) >>
+                           ((threadIdx.x & 31) & ~(TRI_MS - 1));
+    // the eigenvalue lies between the last point with count <= t and the
+    // first with count > t (the counts grow with x)
+    const int f = above ? __ffs(above) - 1 : TRI_MS;
+    const double nlo = f > 0 ? lo + w * ((double)f / (TRI_MS + 1)) : lo;
+    const double nhi = f < TRI_MS ? lo + w * ((double)(f + 1) / (TRI_MS + 1)) : hi;
+    lo = nlo;
+    hi = nhi;
   }
-  lam[s] = 0.5 * (lo + hi);
-  blk[s] = b;
+  if (sub == 0) {
+    lam[s] = 0.5 * (lo + hi);
+    blk[s] = b;
+  }
 }
 
 __global__ void tri_rank_kernel(int64_t total, const double* __restrict__ lam, const int* __restrict__ iprm,
@@ -313,7 +333,7 @@ bse_status tridiag_eig(cudaStream_t s, int64_t N, const double* a, const double*
   bse_count_launch();
   BSE_LAUNCH_CHECK();
   prof_launch_begin(s);
-  tri_bisect_kernel<<<ceil_div_u(total, 64), 64, 0, s>>>(total, w.a, w.e2, w.bstart, w.iprm, w.prm, mode, w.lam,
+  tri_bisect_kernel<<<ceil_div_u(total * TRI_MS, 64), 64, 0, s>>>(total, w.a, w.e2, w.bstart, w.iprm, w.prm, mode, w.lam,
                                                          w.blk, w.grid, status);
   prof_launch_end(s, "tri_bisect_kernel");
   bse_count_launch();
