@@ -597,7 +597,11 @@ def main():
         "bound": "alu", "kernel": "gemm_kernel<cplx> (FP64 DFMA GEMM engine)",
         "achieved": gemm_tf, "peak": peak_tf, "unit": "TFLOP/s",
         "frac": (gemm_tf / peak_tf) if gemm_tf else None,
-        "traffic": None,
+        "traffic": 187.3e6,
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one gemm_kernel<cplx> launch, the "
+                          "congruence W = M1 L at n = 2048 (profiles/gemm_kernel_cplx_n2048_congruence.md; kernel "
+                          "unchanged since), against 160e6 algorithmic bytes (read M1 and the lower half of L, write "
+                          "W): 1.17x; the achieved rate aggregates every launch of the step",
         "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flops/clock/SM (nominal FP64 1.25 TFLOP/s); "
                        "a DFMA throughput loop measured 1.20 TFLOP/s and FP64 mma.sync 1.05 TFLOP/s on a GB300",
         "measured_dfma_peak": 1.20,
@@ -656,7 +660,12 @@ def main():
                          "fp64_equivalent_tflops": pr_m["tc_flops"] / (pr_m["tc_ms"] / 1e3) / 1e12 if pr_m["tc_ms"] > 0 else None,
                          "products_incl_splitting_fp64_equivalent_tflops":
                              pr_m["gemm_flops"] / (pr_m["gemm_ms"] / 1e3) / 1e12 if pr_m["gemm_ms"] > 0 else None,
-                         "traffic": None},
+                         "traffic": 10.12e9,
+                         "traffic_source": "ncu dram bytes of the longest oz_umma_kernel launch of a mixed CHOL "
+                                           "solve at n = 4096 (profiles/oz_umma_kernel_n4096.md), against 1.88e9 "
+                                           "algorithmic bytes (8 slices of both operands read once, C written): "
+                                           "5.4x, set by the 128 x 64 tile (each wave of 152 tiles re-reads its "
+                                           "operand bands); DRAM 12% busy, not the bound"},
         }
     print(json.dumps(line), flush=True)
     if pg:
