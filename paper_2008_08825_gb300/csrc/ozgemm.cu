@@ -560,18 +560,24 @@ struct UmTile {
   bool valid;
 };
 
+// Every role of every CTA evaluates this for each tile it visits, so it uses
+// 32-bit arithmetic (three 32-bit divisions; the tile count stays below 2^31,
+// checked at launch): with 64-bit divisions the 20 warps of a CTA spent as
+// many instructions here as in the folds and the epilogue of a thin product.
 template <typename T>
-__device__ __forceinline__ UmTile um_tile(const GemmParams<T>& p, int64_t L, int64_t ntx, int64_t nty) {
+__device__ __forceinline__ UmTile um_tile(const GemmParams<T>& p, uint32_t L, uint32_t ntx, uint32_t nty) {
   constexpr int XF = sizeof(T) == sizeof(cplx) ? 2 : 1;
   UmTile t;
-  const int64_t per = ntx * nty;
-  t.tz = L / per;
-  const int64_t lin = L - t.tz * per;
-  const int64_t grp = lin / (8 * ntx), first = grp * 8;
-  const int64_t rows = (nty - first) < 8 ? (nty - first) : 8;
-  const int64_t loc = lin % (8 * ntx);
-  const int64_t ty = first + loc % rows, tx = loc / rows;
-  t.i0 = ty * UM_BM, t.jr0 = tx * UM_BN, t.jc0 = t.jr0 / XF;
+  const uint32_t per = ntx * nty, band = 8u * ntx;
+  const uint32_t tz = L / per;
+  const uint32_t lin = L - tz * per;
+  const uint32_t grp = lin / band, first = grp * 8u;
+  const uint32_t rows = (nty - first) < 8u ? (nty - first) : 8u;
+  const uint32_t loc = lin - grp * band;
+  const uint32_t q = loc / rows;
+  const uint32_t ty = first + (loc - q * rows), tx = q;
+  t.tz = tz;
+  t.i0 = (int64_t)ty * UM_BM, t.jr0 = (int64_t)tx * UM_BN, t.jc0 = t.jr0 / XF;
   t.valid = t.i0 < p.m && t.jc0 < p.n && !(p.lowerC && t.jc0 > t.i0 + UM_BM - 1);
   int64_t kb = 0, ke = p.k;
   if (p.triA == TRI_LO) ke = min(ke, t.i0 + UM_BM);
@@ -603,8 +609,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
   constexpr bool CPLX = sizeof(T) == sizeof(cplx);
   const GemmParams<T>& p = z.p;
   if (p.status && *(volatile const int64_t*)p.status) return;
-  const int64_t ntx = (z.ncols_real + UM_BN - 1) / UM_BN, nty = (z.Mp + UM_BM - 1) / UM_BM;
-  const int64_t ntiles = ntx * nty * (p.kchunk > 0 ? (p.k + p.kchunk - 1) / p.kchunk : 1);
+  const uint32_t ntx = (uint32_t)((z.ncols_real + UM_BN - 1) / UM_BN), nty = (uint32_t)((z.Mp + UM_BM - 1) / UM_BM);
+  const uint32_t ntiles = ntx * nty * (uint32_t)(p.kchunk > 0 ? (p.k + p.kchunk - 1) / p.kchunk : 1);
 
   unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(base + UM_STAGES * L::STAGE);  // full[S] empty[S] tfull tempty drain
@@ -639,7 +645,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
   if (warp == 0 && lane == 0) {
     // producer
     bool ok = true;
-    for (int64_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
+    for (uint32_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
       const UmTile t = um_tile(p, Lt, ntx, nty);
       if (!t.valid) continue;
       for (int kt = 0; kt < t.ntile; ++kt, ++issued) {
@@ -668,7 +674,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
     // MMA issuer
     bool ok = true;
     uint32_t g = 0, F = 0;  // k-tiles consumed, folds issued (global)
-    for (int64_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
+    for (uint32_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
       const UmTile t = um_tile(p, Lt, ntx, nty);
       if (!t.valid) continue;
       for (int kt = 0; kt < t.ntile; ++kt, ++g) {
@@ -743,7 +749,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) oz_umma_kernel(const OzArgs<T> 
     release_sets();
     uint32_t F = 0;  // folds consumed (global)
     bool ok = true;
-    for (int64_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
+    for (uint32_t Lt = blockIdx.x; Lt < ntiles && ok; Lt += gridDim.x) {
       const UmTile t = um_tile(p, Lt, ntx, nty);
       if (!t.valid) continue;
       // a column's value = hi 2^-28 + lo 2^-45 in units of the level-2
@@ -1055,6 +1061,10 @@ static bse_status umma_launch(cudaStream_t s, const OzArgs<T>& z, int64_t ncols_
   za.ncols_real = ncols_real;
   const int64_t layers = z.p.kchunk > 0 ? (z.p.k + z.p.kchunk - 1) / z.p.kchunk : 1;
   const int64_t tiles = ((ncols_real + UM_BN - 1) / UM_BN) * ((z.Mp + UM_BM - 1) / UM_BM) * layers;
+  if (tiles >= ((int64_t)1 << 31)) {
+    bse_internal_set_error("tensor-core GEMM: more than 2^31 tiles");
+    return BSE_ERR_ARG;
+  }
   const int64_t sms = oz_device_sms();
   const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
   prof_tc_begin(s);
