@@ -56,6 +56,7 @@ def parse():
                          "event profiling (library profiling level 2), one JSON line each")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched block")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the n = 8192 accuracy block (oracle values)")
+    ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core stages block")
     ap.add_argument("--workload", default="n8192", choices=["n8192", "batched"],
                     help="n8192: the headline solve; batched: 512 uneven instances, lowest 32 pairs")
     return ap.parse_args()
@@ -351,6 +352,47 @@ def batched_inline(dev, h, steps: int, warmup: int, methods=("chol", "svd")):
     return out
 
 
+def ooc_inline(h, n: int = 8192, nb: int = 1024, budget: int = 12, steps: int = 1):
+    """The BLAS3 stages of Alg. 2 (A +- B, Cholesky of A - B, congruence) out of
+    core: the base workload's A and B in pinned host tiles, at most `budget`
+    device tiles of nb x nb, copies overlapped with the tile tasks by the
+    library's executor.  Timed with CUDA events on the tasks' stream (the call
+    returns after its last copy); the rate counts the tile tasks' flops."""
+    import numpy as np
+    import torch
+
+    from paper_2008_08825_gb300 import inputs, ooc
+
+    A, B = inputs.base(n, seed=0)
+    t0 = time.perf_counter()
+    p = ooc.DevicePlan(A, B, nb, budget)
+    prep = time.perf_counter() - t0
+    p.run(handle=h)  # warm-up
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        p.run(handle=h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    L, M = p.results()
+    # spot check against the tile definition: the first tile column of L
+    Af, Bf = inputs.hermitian_full(A[:nb, :nb]), inputs.hermitian_full(B[:nb, :nb])
+    L00 = np.linalg.cholesky(Af - Bf)
+    check = float(np.abs(L[:nb, :nb] - L00).max() / np.abs(L00).max())
+    tf = p.stats["flops"] / t / 1e12
+    return {"seconds": t, "tile_task_tflops": tf, "frac_of_fp64_peak": tf / (fp64_peak() / 1e3),
+            "bytes_moved": p.stats["bytes_moved"], "host_link_gbs": p.stats["bytes_moved"] / t / 1e9,
+            "loads": p.stats["loads"], "stores": p.stats["stores"], "device_tiles": budget,
+            "device_bytes": budget * 16 * nb * nb, "host_prep_s": prep, "l00_rel_err": check,
+            "config": {"workload": f"base n={n} (seed 0), tiles {nb} x {nb}, {budget} device tiles "
+                                   f"({budget * 16 * nb * nb / 1e9:.2f} GB) for a {n // nb} x {n // nb} tile grid; "
+                                   "A +- B, tile Cholesky of A - B, W = (A+B) L, M = L^H W; FP64",
+                       "n": n, "nb": nb}}
+
+
 def accuracy_full_size(At, Bt, h, dev, seed_ok: bool):
     """Accuracy at the bench's n (8192) against the stored oracle omega (tests/golden,
     written by tests/golden/make_c3_oracle.py): the base workload and the
@@ -643,6 +685,8 @@ def main():
         line["batched"] = batched_inline(dev, h, steps=max(1, min(args.steps, 3)), warmup=1)
     if not args.no_accuracy:
         line[f"accuracy_n{n}"] = accuracy_full_size(At, Bt, h, dev, seed_ok=(rank == 0))
+    if not args.no_ooc:
+        line["out_of_core"] = ooc_inline(h, n=n, nb=1024 if n % 1024 == 0 else n // 8, budget=12)
     if sqrt_cmp:
         line["sqrt_vs_chol"] = sqrt_cmp
     if "mixed" in results and precs[0] != "mixed":

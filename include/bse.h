@@ -319,6 +319,90 @@ bse_status bse_profile_read(bse_handle h, bse_profile_data* out);
 int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
 
 /*
+ * Out-of-core tile executor for the BLAS3 stages of Alg. 2 (form A +- B,
+ * step 1's Cholesky factorisation L L^H = A - B and step 2's congruence
+ * M = L^H (A + B) L) when the matrices live in HOST memory: the problem
+ * sizes of Section 4's runtime discussion (n ~ 1e5, 160 GB per complex
+ * matrix) exceed the GPU's memory with A, B, L and M together.
+ *
+ * A run executes a PLAN: a list of operations on nb x nb complex128 tiles
+ * (column-major, leading dimension nb) made by a planner that knows the task
+ * order (the package's ooc.plan: Belady eviction under a tile budget):
+ *   LOAD t     host tile t -> a free device slot (copy stream)
+ *   ALLOC t    a free device slot, zero-filled, becomes tile t (no transfer)
+ *   COMPUTE i  task i on the caller's stream (its tiles must be resident)
+ *   STORE t    device tile t -> host tile t (copy stream)
+ *   FREE t     tile t gives its slot back
+ * Copies and tasks overlap: each slot carries events, a LOAD waits only for
+ * the last task that used its slot, a task only for its own tiles' copies.
+ *
+ * Tasks (out is read and written unless the plan ALLOCs it first):
+ *   FORM_SUM   out = in0 + in1             (tiles of A and B -> A + B)
+ *   FORM_DIFF  out = in0 - in1             (-> A - B)
+ *   POTRF      out = chol(out), lower; the strict upper part is set to 0;
+ *              the tile's inverse conjugate transpose is kept for TRSM
+ *   TRSM       out = out L^{-H}, L the tile in0 (the latest POTRF's tile)
+ *   HERK       out -= in0 in0^H            (lower part of out only)
+ *   GEMM_SUB   out -= in0 in1^H
+ *   GEMM_ACC   out += op(in0) in1, op by flags:
+ *              BSE_OOC_IN0_CONJT   op(in0) = in0^H
+ *              BSE_OOC_IN0_HERM    in0 is a Hermitian diagonal tile stored in
+ *                                  its lower part: op(in0) = tril + tril(-1)^H
+ *              BSE_OOC_IN0_LOWER   in0 is lower triangular (structure mask)
+ *              BSE_OOC_IN1_LOWER   in1 is lower triangular (structure mask)
+ *
+ * nb          tile size, 1 <= nb <= 4096.
+ * host_tiles  ntiles HOST pointers, each to nb*nb complex128 (2 nb^2 doubles);
+ *             page-locked memory lets copies overlap with tasks.  Tiles that
+ *             are only ALLOCed and never stored may be NULL.
+ * ops, nops   the plan, executed in order.
+ * tasks       ntasks task descriptors referenced by COMPUTE.
+ * budget      device tile slots (>= the tiles any one task touches); the
+ *             library allocates budget + 1 slots and scratch for the run in
+ *             the handle's workspace.
+ * info        host, may be NULL: info->info = failing 1-based GLOBAL column
+ *             of a POTRF task that met a non-positive pivot (the plan's
+ *             tile row of that task times nb plus the column in the tile;
+ *             the row is taken from the task's BSE_OOC_ROW(flags) field).
+ * stream      the caller's stream (tasks run on it); the call returns after
+ *             every STORE has completed.
+ * Errors: BSE_ERR_ARG (a plan that is inconsistent: a tile used while not
+ * resident, loaded twice, more than `budget` resident, an index out of
+ * range; nothing is enqueued then), BSE_ERR_NOT_PD_AMINUSB, BSE_ERR_CUDA,
+ * BSE_ERR_NOMEM.  FP64 arithmetic (the GEMM engine) in every task.
+ */
+typedef enum { BSE_OOC_LOAD = 0, BSE_OOC_ALLOC = 1, BSE_OOC_COMPUTE = 2, BSE_OOC_STORE = 3, BSE_OOC_FREE = 4 } bse_ooc_opkind;
+typedef enum {
+  BSE_OOC_FORM_SUM = 0,
+  BSE_OOC_FORM_DIFF = 1,
+  BSE_OOC_POTRF = 2,
+  BSE_OOC_TRSM = 3,
+  BSE_OOC_HERK = 4,
+  BSE_OOC_GEMM_SUB = 5,
+  BSE_OOC_GEMM_ACC = 6
+} bse_ooc_taskkind;
+#define BSE_OOC_IN0_CONJT 1
+#define BSE_OOC_IN0_HERM 2
+#define BSE_OOC_IN0_LOWER 4
+#define BSE_OOC_IN1_LOWER 8
+/* POTRF: tile row k of the task stored in flags bits 8..31 */
+#define BSE_OOC_ROW(flags) ((int64_t)(((uint32_t)(flags)) >> 8))
+typedef struct bse_ooc_op {
+  int32_t kind;  /* bse_ooc_opkind */
+  int32_t arg;   /* tile index (LOAD, ALLOC, STORE, FREE) or task index (COMPUTE) */
+} bse_ooc_op;
+typedef struct bse_ooc_task {
+  int32_t kind;  /* bse_ooc_taskkind */
+  int32_t out;   /* tile written */
+  int32_t in0;   /* tiles read, -1 when unused */
+  int32_t in1;
+  int32_t flags;
+} bse_ooc_task;
+bse_status bse_ooc_run(bse_handle h, int64_t nb, int64_t ntiles, void* const* host_tiles, int64_t nops,
+                       const bse_ooc_op* ops, int64_t ntasks, const bse_ooc_task* tasks, int64_t budget,
+                       bse_info* info, void* stream);
+
+/*
  * Allocation-free Cholesky solve of ONE small problem.  The paper has no
  * counterpart: this entry point serves callers that cannot allocate device
  * memory (device memory wholly held by another allocator's pool; latency-

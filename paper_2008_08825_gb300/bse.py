@@ -86,6 +86,8 @@ def _bind(lib):
         f.restype = ctypes.c_int
     lib.bse_solve_chol_noalloc.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P]
     lib.bse_solve_chol_noalloc.restype = ctypes.c_int
+    lib.bse_ooc_run.argtypes = [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(_Info), _P]
+    lib.bse_ooc_run.restype = ctypes.c_int
     lib.bse_set_option.argtypes = [_P, ctypes.c_int, _I64]
     lib.bse_set_option.restype = ctypes.c_int
     lib.bse_profile_enable.argtypes = [_P, ctypes.c_int]
@@ -348,6 +350,31 @@ def solve_host(A, B, method: str = "chol", il: int | None = None, iu: int | None
                                 max(n, 1), ctypes.byref(info), _P(_stream_ptr(stream)))
     _check(code, info.info)
     return omega, Xt.mT, Yt.mT
+
+
+class OocOp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("arg", ctypes.c_int32)]
+
+
+class OocTask(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("out", ctypes.c_int32), ("in0", ctypes.c_int32), ("in1", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+def ooc_run(nb: int, host_tiles, ops, tasks, budget: int, handle: Handle | None = None, stream=None) -> None:
+    """bse_ooc_run: execute an out-of-core tile plan.
+    host_tiles: list of CPU tensors (nb x nb complex128 tiles stored column-major, e.g. a
+    tile's transpose made contiguous; pinned memory lets copies overlap) or None;
+    ops: list of (kind, arg); tasks: list of (kind, out, in0, in1, flags)."""
+    h = handle or default_handle()
+    ptrs = (ctypes.c_void_p * max(len(host_tiles), 1))(*[t.data_ptr() if t is not None else None
+                                                          for t in host_tiles])
+    op_arr = (OocOp * max(len(ops), 1))(*[OocOp(int(k), int(a)) for k, a in ops])
+    task_arr = (OocTask * max(len(tasks), 1))(*[OocTask(*[int(v) for v in t]) for t in tasks])
+    info = _Info()
+    code = lib().bse_ooc_run(h.ptr, int(nb), len(host_tiles), ptrs, len(ops), op_arr, len(tasks), task_arr,
+                             int(budget), ctypes.byref(info), _P(_stream_ptr(stream)))
+    _check(code, info.info)
 
 
 def _is_colmajor(T: torch.Tensor) -> bool:

@@ -29,6 +29,13 @@
 #include "kernels.cuh"
 #include "prof.cuh"
 
+// ---- ooc.cu ----
+size_t ooc_ws_bytes(int64_t nb, int64_t budget);
+const char* ooc_validate(int64_t nb, int64_t ntiles, void* const* host_tiles, int64_t nops, const bse_ooc_op* ops,
+                         int64_t ntasks, const bse_ooc_task* tasks, int64_t budget, std::string& why);
+bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, void* const* host_tiles, int64_t nops,
+                       const bse_ooc_op* ops, const bse_ooc_task* tasks, int64_t budget, int64_t** status_out);
+
 static thread_local std::string g_err;
 void bse_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
 long long bse_total_launches();
@@ -953,6 +960,37 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
   }
   BSE_CUDA(cudaStreamSynchronize(s));
   return BSE_OK;
+}
+
+bse_status bse_ooc_run(bse_handle h, int64_t nb, int64_t ntiles, void* const* host_tiles, int64_t nops,
+                       const bse_ooc_op* ops, int64_t ntasks, const bse_ooc_task* tasks, int64_t budget,
+                       bse_info* info, void* stream) {
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  std::string why;
+  const char* bad = ooc_validate(nb, ntiles, host_tiles, nops, ops, ntasks, tasks, budget, why);
+  if (bad) return bse_internal_set_error(bad), BSE_ERR_ARG;
+  if (info) *info = bse_info{};
+  if (nops == 0) return BSE_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws;
+  TRY(ensure_ws(h, ooc_ws_bytes(nb, budget), &ws));
+  int64_t* dstatus = nullptr;
+  const bse_status r = ooc_execute(s, ws, nb, ntiles, host_tiles, nops, ops, tasks, budget, &dstatus);
+  if (r != BSE_OK) {
+    cudaStreamSynchronize(s);
+    return r;
+  }
+  BSE_CUDA(cudaMemcpyAsync(h->host_status, dstatus, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  const int64_t code = h->host_status[0], row = h->host_status[2];
+  if (code != 0) {
+    const int64_t col = row >= 0 ? row * nb + h->host_status[1] : h->host_status[1];
+    if (info) info->info = col;
+    char buf[128];
+    snprintf(buf, sizeof buf, "device status %lld (global column %lld)", (long long)code, (long long)col);
+    bse_internal_set_error(buf);
+  }
+  return (bse_status)code;
 }
 
 int64_t bse_launch_count(bse_handle h) {

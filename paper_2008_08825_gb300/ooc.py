@@ -26,6 +26,12 @@ Model
     the budget at every step; ``estimate`` converts a plan into transfer
     bytes and a time bound from a copy bandwidth and a compute rate.
 
+``run_device`` executes a plan on the GPU through the library's tile
+executor (bse_ooc_run): copies on a copy stream, tile tasks on the FP64 GEMM
+engine and the blocked Cholesky, the two overlapped through per-slot events.
+``alg2_stage_tasks`` lists the whole BLAS3 part of Alg. 2 (forming A - B and
+A + B from tiles of A and B, the Cholesky factorisation and the congruence).
+
 The Householder reduction of M is not a tile algorithm in its one-stage form
 (every column needs a matrix-vector product with the whole trailing matrix);
 out of core it needs the two-stage reduction (band reduction in tiles, then
@@ -57,6 +63,24 @@ def _herk_flops(nb):
 
 def _gemm_flops(nb):
     return 8.0 * nb ** 3
+
+
+def form_tasks(nt: int, a: str = "A", b: str = "B", plus: str = "M1", minus: str = "L") -> list:
+    """Lower tiles of A + B and A - B from the lower tiles of A and B (the
+    sums of Alg. 2 before step 1); the outputs are created by the tasks."""
+    tasks = []
+    for j in range(nt):
+        for i in range(j, nt):
+            for kind, out in (("FORM_SUM", plus), ("FORM_DIFF", minus)):
+                tasks.append(Task(kind, ((a, i, j), (b, i, j)), ((out, i, j),), 0.0, fresh=((out, i, j),),
+                                  args={"i": i, "j": j}))
+    return tasks
+
+
+def alg2_stage_tasks(nt: int, nb: int) -> list:
+    """Alg. 2's tile stages in order: M1 = A + B and L := A - B (lower
+    tiles), L L^H = A - B in place, W = M1 L, M = L^H W (lower tiles)."""
+    return form_tasks(nt) + cholesky_tasks(nt, nb, "L") + congruence_tasks(nt, nb, m1="M1", fac="L", w="W", out="M")
 
 
 def cholesky_tasks(nt: int, nb: int, mat: str = "L") -> list:
@@ -167,7 +191,10 @@ def plan(tasks: list, budget: int, keep: set | None = None) -> list:
 
 def _run_task(t: Task, dev: dict):
     a = t.args
-    if t.kind == "POTRF":
+    if t.kind in ("FORM_SUM", "FORM_DIFF"):
+        (x, y), (tile,) = t.reads, t.writes
+        dev[tile] = dev[x] + dev[y] if t.kind == "FORM_SUM" else dev[x] - dev[y]
+    elif t.kind == "POTRF":
         (tile,) = t.writes
         dev[tile] = np.linalg.cholesky(np.tril(dev[tile]) + np.tril(dev[tile], -1).conj().T)
     elif t.kind == "TRSM":
@@ -262,3 +289,108 @@ def assemble(host: dict, name: str, nt: int, nb: int, lower: bool = True) -> np.
                 continue
             M[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] = host[(name, i, j)]
     return M
+
+
+# ---------------------------------------------------------------------------
+# GPU execution through the library's tile executor
+
+OP_KINDS = {"LOAD": 0, "ALLOC": 1, "COMPUTE": 2, "STORE": 3, "FREE": 4}
+TASK_KINDS = {"FORM_SUM": 0, "FORM_DIFF": 1, "POTRF": 2, "TRSM": 3, "HERK": 4, "GEMM": 5, "WGEMM": 6, "MGEMM": 6}
+IN0_CONJT, IN0_HERM, IN0_LOWER, IN1_LOWER = 1, 2, 4, 8
+
+
+def encode(tasks: list, ops: list):
+    """Tile names, executor tasks (kind, out, in0, in1, flags) and executor
+    ops (kind, arg) for a task list and its plan."""
+    names = []
+    index = {}
+
+    def tid(tile):
+        if tile not in index:
+            index[tile] = len(names)
+            names.append(tile)
+        return index[tile]
+
+    enc = []
+    for t in tasks:
+        a = t.args
+        flags = 0
+        ins = list(t.reads)
+        if t.kind == "POTRF":
+            flags = a["k"] << 8
+        elif t.kind == "WGEMM":  # W(i, j) += op(M1 tile) L(k, j)
+            i, j, k = a["i"], a["j"], a["k"]
+            flags = IN0_HERM if i == k else (IN0_CONJT if i < k else 0)
+            if k == j:
+                flags |= IN1_LOWER
+        elif t.kind == "MGEMM":  # M(i, j) += L(k, i)^H W(k, j)
+            flags = IN0_CONJT | (IN0_LOWER if a["k"] == a["i"] else 0)
+        elif t.kind == "TRSM":
+            ins = [t.reads[0]]
+        (out,) = t.writes
+        in0 = tid(ins[0]) if len(ins) > 0 else -1
+        in1 = tid(ins[1]) if len(ins) > 1 else -1
+        enc.append((TASK_KINDS[t.kind], tid(out), in0, in1, flags))
+    eops = []
+    for op in ops:
+        if op.kind == "COMPUTE":
+            eops.append((OP_KINDS["COMPUTE"], op.task))
+        else:
+            eops.append((OP_KINDS[op.kind], tid(op.tile)))
+    return names, enc, eops
+
+
+class DevicePlan:
+    """The BLAS3 stages of Alg. 2 planned for the GPU executor: A and B (n x n
+    Hermitian, lower triangles read, n a multiple of nb) in host tiles, at
+    most `budget` device tiles.  run() executes the plan (repeatable: the
+    input tiles are only read, every other tile is recreated); results()
+    gives L (L L^H = A - B) and M = L^H (A + B) L as dense lower triangles."""
+
+    def __init__(self, A: np.ndarray, B: np.ndarray, nb: int, budget: int, pinned: bool = True):
+        import torch
+
+        n = A.shape[0]
+        if n % nb:
+            raise ValueError("n must be a multiple of nb")
+        self.n, self.nb, self.nt, self.budget = n, nb, n // nb, budget
+        self.tasks = alg2_stage_tasks(self.nt, nb)
+        self.ops = plan(self.tasks, budget, keep={"L", "M"})
+        self.names, self.enc, self.eops = encode(self.tasks, self.ops)
+        self.host = []
+        for name, i, j in self.names:
+            t = torch.empty((nb, nb), dtype=torch.complex128, pin_memory=pinned)
+            if name in ("A", "B"):
+                src = A if name == "A" else B
+                # column-major tile: the row-major tensor holds the tile's transpose
+                t.copy_(torch.from_numpy(np.ascontiguousarray(src[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb].T)))
+            self.host.append(t)
+        est = estimate(self.tasks, self.ops, nb)
+        self.stats = {"loads": est["loads"], "stores": est["stores"], "tiles": len(self.names),
+                      "bytes_moved": est["bytes_moved"], "flops": est["flops"]}
+
+    def run(self, handle=None, stream=None) -> None:
+        from . import bse
+
+        bse.ooc_run(self.nb, self.host, self.eops, self.enc, self.budget, handle=handle, stream=stream)
+
+    def results(self):
+        n, nb, nt = self.n, self.nb, self.nt
+        index = {name: q for q, name in enumerate(self.names)}
+        out = []
+        for mat in ("L", "M"):
+            Mx = np.zeros((n, n), dtype=np.complex128)
+            for i in range(nt):
+                for j in range(i + 1):
+                    Mx[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] = self.host[index[(mat, i, j)]].numpy().T
+            out.append(np.tril(Mx))
+        return out[0], out[1]
+
+
+def run_device(A: np.ndarray, B: np.ndarray, nb: int, budget: int, handle=None, pinned: bool = True):
+    """One GPU execution of the BLAS3 stages of Alg. 2 out of core (see
+    DevicePlan): returns (L, M, statistics of the plan)."""
+    p = DevicePlan(A, B, nb, budget, pinned)
+    p.run(handle)
+    L, M = p.results()
+    return L, M, p.stats

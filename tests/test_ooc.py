@@ -68,3 +68,65 @@ def test_estimate_n1e5():
     assert est["compute_bound"]
     compulsory = (nt * (nt + 1)) * est["tile_bytes"]  # L and M1 in, L and M out (lower tiles)
     assert est["bytes_moved"] <= 3.0 * compulsory
+
+
+@pytest.mark.parametrize("budget", [3, 7, 100])
+def test_alg2_stage_plan_from_a_and_b(budget):
+    # the full tile list of the executor: A - B and A + B formed from tiles of
+    # A and B (lower tiles only), then the factorisation and the congruence
+    n, nb = 192, 32
+    A, B = inputs.base(n, seed=12)
+    nt = n // nb
+    tasks = ooc.alg2_stage_tasks(nt, nb)
+    ops = ooc.plan(tasks, budget, keep={"L", "M"})
+    host = {**ooc.tiles_of(A, nb, "A"), **ooc.tiles_of(B, nb, "B")}
+    stats = ooc.simulate(tasks, ops, host, budget, nb)
+    assert stats["peak"] <= budget
+    Af, Bf = inputs.hermitian_full(A), inputs.hermitian_full(B)
+    L_ref = np.linalg.cholesky(Af - Bf)
+    L = np.tril(ooc.assemble(host, "L", nt, nb))
+    assert np.max(np.abs(L - L_ref)) <= 1e-12 * np.abs(L_ref).max()
+    M_ref = np.tril(L_ref.conj().T @ (Af + Bf) @ L_ref)
+    M = np.tril(ooc.assemble(host, "M", nt, nb))
+    assert np.max(np.abs(M - M_ref)) <= 1e-12 * np.abs(M_ref).max()
+
+
+def test_encode_matches_the_executor_contract():
+    # every COMPUTE names a task whose tiles the plan made resident, the flags
+    # follow the tile positions (diagonal tiles Hermitian or triangular, tiles
+    # above the diagonal read conjugate-transposed), POTRF carries its tile row
+    nt, nb = 5, 16
+    tasks = ooc.alg2_stage_tasks(nt, nb)
+    ops = ooc.plan(tasks, 4, keep={"L", "M"})
+    names, enc, eops = ooc.encode(tasks, ops)
+    assert len(enc) == len(tasks) and len(eops) == len(ops)
+    assert len(set(names)) == len(names)
+    resident = set()
+    for kind, arg in eops:
+        if kind in (0, 1):
+            assert arg not in resident
+            resident.add(arg)
+        elif kind == 4:
+            resident.remove(arg)
+        elif kind == 3:
+            assert arg in resident
+        else:
+            tk, out, in0, in1, flags = enc[arg]
+            assert out in resident and (in0 < 0 or in0 in resident) and (in1 < 0 or in1 in resident)
+            assert out not in (in0, in1)
+    assert not resident
+    for t, (tk, out, in0, in1, flags) in zip(tasks, enc):
+        a = t.args
+        if t.kind == "POTRF":
+            assert tk == 2 and flags >> 8 == a["k"] and names[out] == ("L", a["k"], a["k"])
+        elif t.kind == "WGEMM":
+            i, j, k = a["i"], a["j"], a["k"]
+            assert tk == 6
+            assert bool(flags & ooc.IN0_HERM) == (i == k) and bool(flags & ooc.IN0_CONJT) == (i < k)
+            assert bool(flags & ooc.IN1_LOWER) == (k == j)
+            assert names[in0] == ("M1", max(i, k), min(i, k))
+        elif t.kind == "MGEMM":
+            assert tk == 6 and flags & ooc.IN0_CONJT
+            assert bool(flags & ooc.IN0_LOWER) == (a["k"] == a["i"])
+        elif t.kind in ("FORM_SUM", "FORM_DIFF"):
+            assert names[in0][0] == "A" and names[in1][0] == "B"
