@@ -648,8 +648,7 @@ def main():
         "frac": (gemm_tf / peak_tf) if gemm_tf else None,
         "traffic": 187.3e6,
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one gemm_kernel<cplx> launch, the "
-                          "congruence W = M1 L at n = 2048 (profiles/gemm_kernel_cplx_n2048_congruence.md; kernel "
-                          "unchanged since), against 160e6 algorithmic bytes (read M1 and the lower half of L, write "
+                          "congruence W = M1 L at n = 2048, against 160e6 algorithmic bytes (read M1 and the lower half of L, write "
                           "W): 1.17x; the achieved rate aggregates every launch of the step",
         "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flops/clock/SM (nominal FP64 1.25 TFLOP/s); "
                        "a DFMA throughput loop measured 1.20 TFLOP/s and FP64 mma.sync 1.05 TFLOP/s on a GB300",
@@ -713,7 +712,7 @@ def main():
                              pr_m["gemm_flops"] / (pr_m["gemm_ms"] / 1e3) / 1e12 if pr_m["gemm_ms"] > 0 else None,
                          "traffic": 9.97e9,
                          "traffic_source": "ncu dram bytes of the longest oz_umma_kernel launch of a mixed CHOL "
-                                           "solve at n = 4096 (profiles/oz_umma_kernel_n4096.md), against 1.88e9 "
+                                           "solve at n = 4096 (the refinement product M1 V2), against 1.88e9 "
                                            "algorithmic bytes (8 slices of both operands read once, C written): "
                                            "5.3x, set by the 128 x 64 tile (each wave of 152 tiles re-reads its "
                                            "operand bands); DRAM 11% busy, not the bound"},
