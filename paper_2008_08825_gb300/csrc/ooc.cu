@@ -8,12 +8,11 @@
 //
 // The plan (from the package's planner) is a sequence of LOAD / ALLOC /
 // COMPUTE / STORE / FREE operations; this file validates it on the host,
-// then issues copies on a copy stream and tasks on the caller's stream.
-// Every device slot carries two events: `copied` (its last LOAD, ALLOC or
-// STORE on the copy stream) and `used` (the last task that touched it on
-// the compute stream).  A LOAD waits for `used` of its slot, a task for
-// `copied` of its tiles, a STORE for `used` of its tile: copies of the next
-// tiles run under the current tasks, limited only by the free slots.
+// then issues copies on a copy stream and tasks on three compute streams
+// (the caller's and two more).  Every device slot records its last writer
+// and the reads since as events; each operation waits only for the accesses
+// it conflicts with, so copies of the next tiles run under the current tasks
+// (limited only by the free slots) and independent tile tasks overlap.
 //
 // Tasks use the FP64 GEMM engine and the blocked Cholesky of potrf.cu.  The
 // tile TRSM (X L^H = A) multiplies by the tile's inverse conjugate
@@ -59,6 +58,8 @@ __global__ void ooc_mark_kernel(const int64_t* status, int64_t* mark, int64_t ro
 
 static unsigned ooc_blocks(int64_t count) { return ceil_div_u(count, 256); }
 
+constexpr int OOC_STREAMS = 3;  // compute streams (the caller's and two more)
+
 #define OOC_LAUNCH_CHECK()                                      \
   do {                                                          \
     bse_count_launch();                                         \
@@ -70,7 +71,7 @@ size_t ooc_ws_bytes(int64_t nb, int64_t budget) {
   const size_t al = 256;
   auto up = [&](size_t b) { return (b + al - 1) / al * al; };
   return up(tile) * (size_t)(budget + 1)      // slots, one spare
-         + 2 * up(tile)                       // inverse, Hermitian expansion
+         + (1 + OOC_STREAMS) * up(tile)       // inverse, a Hermitian expansion per compute stream
          + up(sizeof(cplx) * chol_linv_elems(nb))  // diagonal-block inverses
          + up(4 * sizeof(int64_t))            // status word, failing tile row
          + al;
@@ -151,34 +152,51 @@ const char* ooc_validate(int64_t nb, int64_t ntiles, void* const* host_tiles, in
 
 namespace {
 
-struct Slots {
-  std::vector<cplx*> ptr;
-  std::vector<cudaEvent_t> copied, used;
-  ~Slots() {
-    for (cudaEvent_t e : copied)
-      if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : used)
-      if (e) cudaEventDestroy(e);
+// Events made during one run, destroyed at its end (recorded work may still
+// be pending then; CUDA releases such an event once its work completes).
+struct EventPool {
+  std::vector<cudaEvent_t> all;
+  cudaError_t make(cudaEvent_t* e) {
+    const cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    if (r == cudaSuccess) all.push_back(*e);
+    return r;
+  }
+  ~EventPool() {
+    for (cudaEvent_t e : all) cudaEventDestroy(e);
   }
 };
 
-// The copy stream is drained before the executor returns, on every path:
-// host tiles are not touched by this call after it returns.
-struct StreamHolder {
-  cudaStream_t s = nullptr;
-  ~StreamHolder() {
-    if (s) {
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
+// Streams created for one run are drained and destroyed before the executor
+// returns, on every path: host tiles are not touched after the call returns.
+struct StreamSet {
+  std::vector<cudaStream_t> v;
+  ~StreamSet() {
+    for (cudaStream_t x : v) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
     }
   }
 };
 
+// One device buffer's accesses in flight: its last writer and the reads
+// issued since that write.
+struct Hazard {
+  cudaEvent_t wr = nullptr;
+  std::vector<cudaEvent_t> rd;
+};
+
 }  // namespace
 
-// Issues the plan and returns once the copy stream has drained (the tasks'
-// stream waits for the last copy; the caller synchronises it and reads the
+// Issues the plan and returns once the created streams have drained (the
+// caller's stream waits for them; the caller synchronises it and reads the
 // status word at `status`, the failing tile row at `status + 2`).
+//
+// Tasks are dealt round-robin to OOC_STREAMS compute streams, copies go to
+// one copy stream; every ordering the plan implies is an event wait: a task
+// waits for the last writer of each tile it touches and, for the tile it
+// writes, for the reads issued since; a LOAD into a slot waits for the last
+// writer and readers of the slot's previous tile.  Independent tile tasks
+// then overlap, which fills the SMs that one tile product leaves idle.
 bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, void* const* host_tiles, int64_t nops,
                        const bse_ooc_op* ops, const bse_ooc_task* tasks, int64_t budget, int64_t** status_out) {
   const size_t al = 256;
@@ -186,20 +204,18 @@ bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, voi
   const size_t tile_b = sizeof(cplx) * (size_t)nb * (size_t)nb;
   char* p = (char*)(((uintptr_t)ws + al - 1) / al * al);
   const int nslots = (int)budget + 1;
-  Slots sl;
-  sl.ptr.resize((size_t)nslots);
-  sl.copied.assign((size_t)nslots, nullptr);
-  sl.used.assign((size_t)nslots, nullptr);
+  std::vector<cplx*> slot((size_t)nslots);
   for (int i = 0; i < nslots; ++i) {
-    sl.ptr[(size_t)i] = (cplx*)p;
+    slot[(size_t)i] = (cplx*)p;
     p += up(tile_b);
-    BSE_CUDA(cudaEventCreateWithFlags(&sl.copied[(size_t)i], cudaEventDisableTiming));
-    BSE_CUDA(cudaEventCreateWithFlags(&sl.used[(size_t)i], cudaEventDisableTiming));
   }
-  cplx* Xinv = (cplx*)p;
+  cplx* Xinv = (cplx*)p;  // L^{-H} of the latest POTRF tile
   p += up(tile_b);
-  cplx* F = (cplx*)p;
-  p += up(tile_b);
+  cplx* F[OOC_STREAMS];  // Hermitian expansion, one per compute stream
+  for (int i = 0; i < OOC_STREAMS; ++i) {
+    F[i] = (cplx*)p;
+    p += up(tile_b);
+  }
   cplx* Linv = (cplx*)p;
   p += up(sizeof(cplx) * chol_linv_elems(nb));
   int64_t* status = (int64_t*)p;  // [0] code, [1] info, [2] failing tile row
@@ -207,23 +223,35 @@ bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, voi
   BSE_CUDA(cudaMemsetAsync(status, 0, 2 * sizeof(int64_t), s));
   BSE_CUDA(cudaMemsetAsync(status + 2, 0xff, sizeof(int64_t), s));
 
-  StreamHolder cs;
-  BSE_CUDA(cudaStreamCreateWithFlags(&cs.s, cudaStreamNonBlocking));
-  cudaEvent_t start = nullptr, done = nullptr;
-  BSE_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-  BSE_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-  struct EvHolder {
-    cudaEvent_t& a;
-    cudaEvent_t& b;
-    ~EvHolder() {
-      if (a) cudaEventDestroy(a);
-      if (b) cudaEventDestroy(b);
-    }
-  } evh{start, done};
-  // the copy stream starts after the caller's earlier work (it may still use
-  // this workspace)
+  EventPool evp;
+  StreamSet made;
+  cudaStream_t cst[OOC_STREAMS];
+  cst[0] = s;
+  for (int i = 0; i < OOC_STREAMS; ++i) {  // OOC_STREAMS - 1 compute streams and the copy stream
+    cudaStream_t x;
+    BSE_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    made.v.push_back(x);
+    if (i + 1 < OOC_STREAMS) cst[i + 1] = x;
+  }
+  cudaStream_t cs = made.v.back();
+  // every stream starts after the caller's earlier work and the status reset
+  // (earlier work on s may still use this workspace)
+  cudaEvent_t start;
+  BSE_CUDA(evp.make(&start));
   BSE_CUDA(cudaEventRecord(start, s));
-  BSE_CUDA(cudaStreamWaitEvent(cs.s, start, 0));
+  for (cudaStream_t x : made.v) BSE_CUDA(cudaStreamWaitEvent(x, start, 0));
+
+  std::vector<Hazard> hz((size_t)nslots);
+  Hazard inv;  // Xinv and Linv
+  auto wait_write = [&](cudaStream_t st, const Hazard& h) -> cudaError_t {
+    return h.wr ? cudaStreamWaitEvent(st, h.wr, 0) : cudaSuccess;
+  };
+  auto wait_all = [&](cudaStream_t st, const Hazard& h) -> cudaError_t {
+    cudaError_t r = wait_write(st, h);
+    for (cudaEvent_t e : h.rd)
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(st, e, 0);
+    return r;
+  };
 
   std::vector<int> free_slots;
   for (int i = nslots - 2; i >= 0; --i) free_slots.push_back(i);
@@ -231,6 +259,7 @@ bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, voi
   std::vector<int> slot_of((size_t)ntiles, -1);
   const cplx one = mkc(1.0, 0.0), mone = mkc(-1.0, 0.0);
   const int64_t nn = nb * nb;
+  int turn = 0;
 
   for (int64_t i = 0; i < nops; ++i) {
     const int kind = ops[i].kind;
@@ -239,77 +268,89 @@ bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, voi
       const int q = free_slots.back();
       free_slots.pop_back();
       slot_of[(size_t)a] = q;
-      BSE_CUDA(cudaStreamWaitEvent(cs.s, sl.used[(size_t)q], 0));
+      BSE_CUDA(wait_all(cs, hz[(size_t)q]));
       if (kind == BSE_OOC_LOAD)
-        BSE_CUDA(cudaMemcpyAsync(sl.ptr[(size_t)q], host_tiles[a], tile_b, cudaMemcpyHostToDevice, cs.s));
+        BSE_CUDA(cudaMemcpyAsync(slot[(size_t)q], host_tiles[a], tile_b, cudaMemcpyHostToDevice, cs));
       else
-        BSE_CUDA(cudaMemsetAsync(sl.ptr[(size_t)q], 0, tile_b, cs.s));
-      BSE_CUDA(cudaEventRecord(sl.copied[(size_t)q], cs.s));
+        BSE_CUDA(cudaMemsetAsync(slot[(size_t)q], 0, tile_b, cs));
+      cudaEvent_t e;
+      BSE_CUDA(evp.make(&e));
+      BSE_CUDA(cudaEventRecord(e, cs));
+      hz[(size_t)q].wr = e;
+      hz[(size_t)q].rd.clear();
     } else if (kind == BSE_OOC_STORE) {
       const int q = slot_of[(size_t)a];
-      BSE_CUDA(cudaStreamWaitEvent(cs.s, sl.used[(size_t)q], 0));
-      BSE_CUDA(cudaMemcpyAsync(host_tiles[a], sl.ptr[(size_t)q], tile_b, cudaMemcpyDeviceToHost, cs.s));
-      BSE_CUDA(cudaEventRecord(sl.copied[(size_t)q], cs.s));
+      BSE_CUDA(wait_write(cs, hz[(size_t)q]));
+      BSE_CUDA(cudaMemcpyAsync(host_tiles[a], slot[(size_t)q], tile_b, cudaMemcpyDeviceToHost, cs));
+      cudaEvent_t e;
+      BSE_CUDA(evp.make(&e));
+      BSE_CUDA(cudaEventRecord(e, cs));
+      hz[(size_t)q].rd.push_back(e);
     } else if (kind == BSE_OOC_FREE) {
       free_slots.push_back(slot_of[(size_t)a]);
       slot_of[(size_t)a] = -1;
     } else {  // COMPUTE
       const bse_ooc_task& t = tasks[a];
+      const int si = turn;
+      turn = (turn + 1) % OOC_STREAMS;
+      cudaStream_t st = cst[si];
       const int qo = slot_of[(size_t)t.out];
       const int q0 = t.in0 >= 0 && task_needs(t.kind, 0) ? slot_of[(size_t)t.in0] : -1;
       const int q1 = t.in1 >= 0 && task_needs(t.kind, 1) ? slot_of[(size_t)t.in1] : -1;
-      for (int q : {qo, q0, q1})
-        if (q >= 0) BSE_CUDA(cudaStreamWaitEvent(s, sl.copied[(size_t)q], 0));
-      cplx* O = sl.ptr[(size_t)qo];
-      const cplx* I0 = q0 >= 0 ? sl.ptr[(size_t)q0] : nullptr;
-      const cplx* I1 = q1 >= 0 ? sl.ptr[(size_t)q1] : nullptr;
-      int q_out_final = qo;
+      const bool trsm = t.kind == BSE_OOC_TRSM, potrf = t.kind == BSE_OOC_POTRF;
+      // the tile written: out, or for TRSM the spare slot that takes its place
+      const int qw = trsm ? spare : qo;
+      BSE_CUDA(wait_all(st, hz[(size_t)qw]));
+      if (trsm) BSE_CUDA(wait_write(st, hz[(size_t)qo]));
+      for (int q : {q0, q1})
+        if (q >= 0) BSE_CUDA(wait_write(st, hz[(size_t)q]));
+      if (potrf) BSE_CUDA(wait_all(st, inv));
+      if (trsm) BSE_CUDA(wait_write(st, inv));
+      cplx* O = slot[(size_t)qo];
+      const cplx* I0 = q0 >= 0 ? slot[(size_t)q0] : nullptr;
+      const cplx* I1 = q1 >= 0 ? slot[(size_t)q1] : nullptr;
       switch (t.kind) {
         case BSE_OOC_FORM_SUM:
         case BSE_OOC_FORM_DIFF:
-          ooc_form_kernel<<<ooc_blocks(nn), 256, 0, s>>>(nn, I0, I1, t.kind == BSE_OOC_FORM_SUM ? 1.0 : -1.0, O,
-                                                         status);
+          ooc_form_kernel<<<ooc_blocks(nn), 256, 0, st>>>(nn, I0, I1, t.kind == BSE_OOC_FORM_SUM ? 1.0 : -1.0, O,
+                                                          status);
           OOC_LAUNCH_CHECK();
           break;
         case BSE_OOC_POTRF: {
-          bse_status r = potrf_lower(s, nb, O, nb, Linv, status, BSE_ERR_NOT_PD_AMINUSB);
+          bse_status r = potrf_lower(st, nb, O, nb, Linv, status, BSE_ERR_NOT_PD_AMINUSB);
           if (r) return r;
-          ooc_mark_kernel<<<1, 1, 0, s>>>(status, status + 2, BSE_OOC_ROW(t.flags));
+          ooc_mark_kernel<<<1, 1, 0, st>>>(status, status + 2, BSE_OOC_ROW(t.flags));
           OOC_LAUNCH_CHECK();
-          ooc_zero_upper_kernel<<<ooc_blocks(nn), 256, 0, s>>>(nb, O, status);
+          ooc_zero_upper_kernel<<<ooc_blocks(nn), 256, 0, st>>>(nb, O, status);
           OOC_LAUNCH_CHECK();
-          ooc_identity_kernel<<<ooc_blocks(nn), 256, 0, s>>>(nb, Xinv);
+          ooc_identity_kernel<<<ooc_blocks(nn), 256, 0, st>>>(nb, Xinv);
           OOC_LAUNCH_CHECK();
-          r = trsm_lower_conjtrans(s, nb, nb, O, nb, Linv, Xinv, nb, status);  // Xinv = L^{-H}
+          r = trsm_lower_conjtrans(st, nb, nb, O, nb, Linv, Xinv, nb, status);  // Xinv = L^{-H}
           if (r) return r;
           break;
         }
         case BSE_OOC_TRSM: {
-          // spare = out L^{-H} (upper triangular factor), then spare and out swap
-          BSE_CUDA(cudaStreamWaitEvent(s, sl.copied[(size_t)spare], 0));
+          // spare = out L^{-H} (upper triangular factor); spare then takes out's place
           GemmParams<cplx> g = gemm_params<cplx>(nb, nb, nb, OPN, O, nb, OPN, Xinv, nb, one, mkc(0.0, 0.0),
-                                                 sl.ptr[(size_t)spare], nb);
+                                                 slot[(size_t)spare], nb);
           g.triB = TRI_UP;
           g.status = status;
-          bse_status r = gemm_z(s, g);
+          bse_status r = gemm_z(st, g);
           if (r) return r;
-          q_out_final = spare;
-          slot_of[(size_t)t.out] = spare;
-          spare = qo;
           break;
         }
         case BSE_OOC_HERK: {
           GemmParams<cplx> g = gemm_params<cplx>(nb, nb, nb, OPN, I0, nb, OPC, I0, nb, mone, one, O, nb);
           g.lowerC = 1;
           g.status = status;
-          bse_status r = gemm_z(s, g);
+          bse_status r = gemm_z(st, g);
           if (r) return r;
           break;
         }
         case BSE_OOC_GEMM_SUB: {
           GemmParams<cplx> g = gemm_params<cplx>(nb, nb, nb, OPN, I0, nb, OPC, I1, nb, mone, one, O, nb);
           g.status = status;
-          bse_status r = gemm_z(s, g);
+          bse_status r = gemm_z(st, g);
           if (r) return r;
           break;
         }
@@ -318,10 +359,10 @@ bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, voi
           int opA = (t.flags & BSE_OOC_IN0_CONJT) ? OPC : OPN;
           int triA = TRI_NONE;
           if (t.flags & BSE_OOC_IN0_HERM) {
-            BSE_CUDA(cudaMemcpyAsync(F, I0, tile_b, cudaMemcpyDeviceToDevice, s));
-            bse_status r = hermitian_fill_upper(s, nb, F, nb);
+            BSE_CUDA(cudaMemcpyAsync(F[si], I0, tile_b, cudaMemcpyDeviceToDevice, st));
+            bse_status r = hermitian_fill_upper(st, nb, F[si], nb);
             if (r) return r;
-            Aop = F;
+            Aop = F[si];
           } else if (t.flags & BSE_OOC_IN0_LOWER) {
             triA = opA == OPN ? TRI_LO : TRI_UP;  // structure of op(in0)
           }
@@ -329,20 +370,38 @@ bse_status ooc_execute(cudaStream_t s, void* ws, int64_t nb, int64_t ntiles, voi
           g.triA = triA;
           g.triB = (t.flags & BSE_OOC_IN1_LOWER) ? TRI_LO : TRI_NONE;
           g.status = status;
-          bse_status r = gemm_z(s, g);
+          bse_status r = gemm_z(st, g);
           if (r) return r;
           break;
         }
         default:
           break;
       }
-      for (int q : {q_out_final, q0, q1})
-        if (q >= 0) BSE_CUDA(cudaEventRecord(sl.used[(size_t)q], s));
-      if (q_out_final != qo) BSE_CUDA(cudaEventRecord(sl.used[(size_t)qo], s));
+      cudaEvent_t e;
+      BSE_CUDA(evp.make(&e));
+      BSE_CUDA(cudaEventRecord(e, st));
+      hz[(size_t)qw].wr = e;
+      hz[(size_t)qw].rd.clear();
+      for (int q : {q0, q1})
+        if (q >= 0) hz[(size_t)q].rd.push_back(e);
+      if (potrf) {
+        inv.wr = e;
+        inv.rd.clear();
+      }
+      if (trsm) {
+        hz[(size_t)qo].rd.push_back(e);
+        inv.rd.push_back(e);
+        slot_of[(size_t)t.out] = spare;
+        spare = qo;
+      }
     }
   }
-  // the caller's stream ends after the last copy
-  BSE_CUDA(cudaEventRecord(done, cs.s));
-  BSE_CUDA(cudaStreamWaitEvent(s, done, 0));
+  // the caller's stream ends after every other stream's last operation
+  for (cudaStream_t x : made.v) {
+    cudaEvent_t e;
+    BSE_CUDA(evp.make(&e));
+    BSE_CUDA(cudaEventRecord(e, x));
+    BSE_CUDA(cudaStreamWaitEvent(s, e, 0));
+  }
   return BSE_OK;
 }
