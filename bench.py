@@ -352,12 +352,13 @@ def batched_inline(dev, h, steps: int, warmup: int, methods=("chol", "svd")):
     return out
 
 
-def ooc_inline(h, n: int = 8192, nb: int = 1024, budget: int = 12, steps: int = 1):
+def ooc_inline(h, n: int = 8192, nb: int = 2048, budget: int = 12, steps: int = 1):
     """The BLAS3 stages of Alg. 2 (A +- B, Cholesky of A - B, congruence) out of
     core: the base workload's A and B in pinned host tiles, at most `budget`
     device tiles of nb x nb, copies overlapped with the tile tasks by the
-    library's executor.  Timed with CUDA events on the tasks' stream (the call
-    returns after its last copy); the rate counts the tile tasks' flops."""
+    library's executor.  Timed with CUDA events on the caller's stream (the call
+    returns after its last copy); the rate counts the tile tasks' useful flops
+    (triangular tiles at half)."""
     import numpy as np
     import torch
 
@@ -685,7 +686,7 @@ def main():
     if not args.no_accuracy:
         line[f"accuracy_n{n}"] = accuracy_full_size(At, Bt, h, dev, seed_ok=(rank == 0))
     if not args.no_ooc:
-        line["out_of_core"] = ooc_inline(h, n=n, nb=1024 if n % 1024 == 0 else n // 8, budget=12)
+        line["out_of_core"] = ooc_inline(h, n=n, nb=2048 if n % 2048 == 0 else n // 4, budget=12)
     if sqrt_cmp:
         line["sqrt_vs_chol"] = sqrt_cmp
     if "mixed" in results and precs[0] != "mixed":

@@ -107,12 +107,14 @@ def congruence_tasks(nt: int, nb: int, m1: str = "M1", fac: str = "L", w: str = 
         for i in range(nt):
             for k in range(j, nt):  # L(k, j) = 0 for k < j
                 a = (m1, i, k) if i >= k else (m1, k, i)  # the stored lower tile, transposed when i < k
-                tasks.append(Task("WGEMM", (a, (fac, k, j)), ((w, i, j),), _gemm_flops(nb),
+                # L(j, j) is lower triangular: half the multiply-adds
+                tasks.append(Task("WGEMM", (a, (fac, k, j)), ((w, i, j),), _gemm_flops(nb) / (2 if k == j else 1),
                                   fresh=((w, i, j),) if k == j else (), args={"i": i, "j": j, "k": k}))
     for j in range(nt):
         for i in range(j, nt):
             for k in range(i, nt):  # L(k, i) = 0 for k < i
-                tasks.append(Task("MGEMM", ((fac, k, i), (w, k, j)), ((out, i, j),), _gemm_flops(nb),
+                tasks.append(Task("MGEMM", ((fac, k, i), (w, k, j)), ((out, i, j),),
+                                  _gemm_flops(nb) / (2 if k == i else 1),
                                   fresh=((out, i, j),) if k == i else (), args={"i": i, "j": j, "k": k}))
     return tasks
 
