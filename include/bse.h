@@ -333,8 +333,12 @@ int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
  *   COMPUTE i  task i on the caller's stream (its tiles must be resident)
  *   STORE t    device tile t -> host tile t (copy stream)
  *   FREE t     tile t gives its slot back
- * Copies and tasks overlap: each slot carries events, a LOAD waits only for
- * the last task that used its slot, a task only for its own tiles' copies.
+ * Copies run on a copy stream and tasks on three compute streams (the
+ * caller's and two the call creates), ordered only by events on the tiles
+ * they share (a task waits for its tiles' last writers and, for the tile it
+ * writes, for the reads since; a LOAD waits for the previous tile of its
+ * slot): copies overlap tasks and independent tasks overlap each other.
+ * The results do not depend on that overlap (same bits on every run).
  *
  * Tasks (out is read and written unless the plan ALLOCs it first):
  *   FORM_SUM   out = in0 + in1             (tiles of A and B -> A + B)
@@ -364,8 +368,9 @@ int64_t bse_profile_kernels(bse_handle h, char* buf, size_t len);
  *             of a POTRF task that met a non-positive pivot (the plan's
  *             tile row of that task times nb plus the column in the tile;
  *             the row is taken from the task's BSE_OOC_ROW(flags) field).
- * stream      the caller's stream (tasks run on it); the call returns after
- *             every STORE has completed.
+ * stream      the caller's stream (one of the compute streams; it waits for
+ *             the others at the end); the call returns after every STORE
+ *             has completed.
  * Errors: BSE_ERR_ARG (a plan that is inconsistent: a tile used while not
  * resident, loaded twice, more than `budget` resident, an index out of
  * range; nothing is enqueued then), BSE_ERR_NOT_PD_AMINUSB, BSE_ERR_CUDA,
