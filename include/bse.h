@@ -17,8 +17,9 @@
  *   - Complex matrices are complex128 stored as interleaved (re, im) doubles,
  *     column-major: element (i, j) of a matrix with leading dimension ld is at
  *     p[2*(i + j*ld)] (real) and p[2*(i + j*ld) + 1] (imaginary).  ld >= max(1, n).
- *   - Unless a name ends in _host, every data pointer is a DEVICE pointer,
- *     allocated and owned by the caller.  Inputs are never modified.
+ *   - Unless a name ends in _host (or is bse_ooc_run's host tiles), every data
+ *     pointer is a DEVICE pointer, allocated and owned by the caller.  Inputs
+ *     are never modified.
  *   - Only the lower triangle (diagonal included) of the Hermitian inputs A, B
  *     is read; the imaginary parts of their diagonals are ignored.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
