@@ -965,10 +965,11 @@ bse_status bse_solve_host(bse_handle h, int method, int64_t n, const double* A, 
 bse_status bse_ooc_run(bse_handle h, int64_t nb, int64_t ntiles, void* const* host_tiles, int64_t nops,
                        const bse_ooc_op* ops, int64_t ntasks, const bse_ooc_task* tasks, int64_t budget,
                        bse_info* info, void* stream) {
-  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
+  // the plan is checked on the host before anything else (no CUDA call)
   std::string why;
   const char* bad = ooc_validate(nb, ntiles, host_tiles, nops, ops, ntasks, tasks, budget, why);
   if (bad) return bse_internal_set_error(bad), BSE_ERR_ARG;
+  if (!h) return bse_internal_set_error("NULL handle"), BSE_ERR_ARG;
   if (info) *info = bse_info{};
   if (nops == 0) return BSE_OK;
   cudaStream_t s = (cudaStream_t)stream;

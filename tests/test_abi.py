@@ -75,3 +75,38 @@ def test_noalloc_host_checks_need_no_gpu(lib):
     assert lib.bse_solve_chol_noalloc(8, 0, None, None, None, None, None, None, None) == 0
     assert lib.bse_solve_chol_noalloc(0, 0, None, None, None, None, None, None, None) == 7
     assert lib.bse_solve_chol_noalloc(8, 2, None, None, None, None, None, None, None) == 1  # NULL pointers
+
+
+def test_out_of_core_plan_checks_need_no_gpu(lib):
+    """bse_ooc_run checks a plan on the host before any CUDA call: residency,
+    the tile budget, indices and the TRSM/POTRF pairing are refused with an
+    argument error naming the op; a consistent plan then meets the handle
+    check (NULL here) and nothing runs."""
+    from paper_2008_08825_gb300 import ooc
+
+    Op, Task = bse.OocOp, bse.OocTask
+    tiles = (ctypes.c_void_p * 3)(1, 2, 3)  # never dereferenced: every call below is refused first
+    gemm = Task(ooc.TASK_KINDS["GEMM"], 2, 0, 1, 0)
+    trsm = Task(ooc.TASK_KINDS["TRSM"], 1, 0, -1, 0)
+
+    def run(ops, tasks, budget, nb=16):
+        o = (Op * max(len(ops), 1))(*[Op(k, a) for k, a in ops])
+        t = (Task * max(len(tasks), 1))(*tasks)
+        return lib.bse_ooc_run(None, nb, 3, tiles, len(ops), o, len(tasks), t, budget, None, None)
+
+    cases = [
+        ([(2, 0)], [gemm], 3, "not resident"),
+        ([(0, 0), (0, 1), (0, 2)], [gemm], 2, "budget"),
+        ([(0, 0), (0, 0)], [gemm], 3, "already resident"),
+        ([(3, 1)], [gemm], 3, "not resident"),
+        ([(0, 0), (0, 1), (0, 2), (2, 5)], [gemm], 3, "task index"),
+        ([(0, 7)], [gemm], 3, "out of range"),
+        ([(0, 0), (0, 1), (2, 0)], [trsm], 3, "POTRF"),
+        ([(0, 0), (4, 0), (4, 0)], [gemm], 3, "not resident"),
+    ]
+    for ops, tasks, budget, what in cases:
+        assert run(ops, tasks, budget) == 1, ops
+        assert what.encode() in lib.bse_last_error(), (ops, lib.bse_last_error())
+    assert run([(0, 0)], [gemm], 3, nb=0) == 1 and b"nb" in lib.bse_last_error()
+    assert run([(0, 0), (0, 1), (0, 2), (2, 0), (3, 2), (4, 0), (4, 1), (4, 2)], [gemm], 3) == 1
+    assert b"handle" in lib.bse_last_error()
